@@ -1,0 +1,192 @@
+"""CPU oracle for the block staircase iteration -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package.  The GPU library never calls it, and it
+shares no code with the GPU library: its arithmetic lives in ``oracle.c``
+(plain FP64 C, no FP contraction), wrapped here with ctypes and numpy.
+
+What it computes (arXiv 2302.07551):
+  * Eq. (1): the stationary vector pi of Q^T pi = 0, pi >= 0, e^T pi = 1;
+  * Sect. 2: regular splittings T = Q^T = M - N -- stair matrices of type 1
+    and 2, block Gauss-Seidel, block Jacobi -- and the normalised scheme of
+    Eq. (2);
+  * Algorithm 2: one staircase sweep in three steps (off-staircase products,
+    diagonal-only rows, coupled rows), normalisation and the L1 step error;
+  * Sect. 3: the stopping rule (step error <= eps or k >= maxit), plus the
+    residual ||Q^T pi||_1 <= tol test used by the GPU solver.
+
+Pins (tests/test_oracle_*.py, CPU only): Example 1 and Example 2 spectra,
+dense direct solves, the birth-death closed form, invariants, LU
+reconstruction, equal STAIR/BGS spectra on block-tridiagonal matrices and
+Young's relation with block Jacobi, observed contraction vs the eigenvalue.
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_SO = os.path.join(_HERE, "liboracle.so")
+_lib = None
+
+STAIR1, STAIR2, BGS, BJ = 1, 2, 3, 4
+METHODS = {"stair1": STAIR1, "stair2": STAIR2, "bgs": BGS, "bj": BJ}
+
+
+def build(verbose=False):
+    """Compile liboracle.so in place (gcc -O2 -ffp-contract=off -fopenmp)."""
+    cmd = ["gcc", "-O2", "-ffp-contract=off", "-fopenmp", "-fPIC", "-shared",
+           "-o", _SO, _SRC, "-lm"]
+    if verbose:
+        print(" ".join(cmd))
+    subprocess.check_call(cmd)
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        build()
+    lib = ctypes.CDLL(_SO)
+    vp, i64, i32, dbl = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.or_build_T.argtypes = [i64, i32, vp, vp, vp, vp, vp, vp]
+    lib.or_build_T.restype = None
+    lib.or_lu.argtypes = [i32, vp, vp]
+    lib.or_lu.restype = i32
+    lib.or_lu_solve.argtypes = [i32, vp, vp, vp]
+    lib.or_lu_solve.restype = None
+    lib.or_factor.argtypes = [i64, i32, vp, vp, vp]
+    lib.or_factor.restype = i64
+    lib.or_sweep.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp]
+    lib.or_sweep.restype = i32
+    lib.or_residual.argtypes = [i64, i32, vp, vp, vp, vp]
+    lib.or_residual.restype = dbl
+    lib.or_solve.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
+    lib.or_solve.restype = i64
+    lib.or_threads.argtypes = [i32]
+    lib.or_threads.restype = i32
+    _lib = lib
+    return lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def _c64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def threads(n=0):
+    """Set (n > 0) and return the oracle's OpenMP thread count."""
+    return _load().or_threads(int(n))
+
+
+class Chain:
+    """Blocks of T = Q^T and their LU factors for one block-tridiagonal chain.
+
+    ``dn, loc, up`` are generator blocks of Q, shape (L, m, m), row-major:
+    Q[l, l-1], Q[l, l], Q[l, l+1].
+    """
+
+    def __init__(self, dn, loc, up):
+        dn, loc, up = _c64(dn), _c64(loc), _c64(up)
+        L, m, m2 = loc.shape
+        assert m == m2 and dn.shape == loc.shape == up.shape
+        self.L, self.m, self.N = L, m, L * m
+        self.Tlo = np.empty_like(loc)
+        self.Tdd = np.empty_like(loc)
+        self.Tup = np.empty_like(loc)
+        _load().or_build_T(L, m, _p(dn), _p(loc), _p(up), _p(self.Tlo), _p(self.Tdd), _p(self.Tup))
+        self.LU = np.empty_like(loc)
+        self.piv = np.empty((L, m), np.int32)
+        self.swaps = _load().or_factor(L, m, _p(self.Tdd), _p(self.LU), _p(self.piv))
+        if self.swaps < 0:
+            raise ValueError("singular diagonal block")
+
+    def sweep(self, x, method=STAIR1):
+        """Unnormalised z = M^{-1} N x for the chosen splitting."""
+        x = _c64(x).reshape(-1)
+        z = np.empty(self.N)
+        rc = _load().or_sweep(self.L, self.m, int(method), _p(self.Tlo), _p(self.Tup),
+                              _p(self.LU), _p(self.piv), _p(x), _p(z))
+        if rc != 0:
+            raise ValueError("bad method")
+        return z
+
+    def normalised_sweep(self, x, method=STAIR1):
+        """One step of Eq. (2): returns (z / e^T z, e^T z, ||z/e^T z - x||_1)."""
+        x = _c64(x).reshape(-1)
+        z = self.sweep(x, method)
+        s = float(np.sum(z)) if self.N < 2 else float(_seqsum(z))
+        pi = z / s
+        return pi, s, float(np.sum(np.abs(pi - x)))
+
+    def sweeps(self, x, k, method=STAIR1):
+        """k normalised sweeps from x; returns the final iterate."""
+        x = _c64(x).reshape(-1).copy()
+        tmp = np.zeros(2)
+        if k > 0:
+            _load().or_solve(self.L, self.m, int(method), _p(self.Tlo), _p(self.Tdd), _p(self.Tup),
+                             _p(self.LU), _p(self.piv), _p(x), 0.0, 0.0, int(k), 1, None, _p(tmp))
+        return x
+
+    def residual(self, x):
+        """||Q^T x||_1 computed directly from the blocks."""
+        x = _c64(x).reshape(-1)
+        return _load().or_residual(self.L, self.m, _p(self.Tlo), _p(self.Tdd), _p(self.Tup), _p(x))
+
+    def solve(self, x0=None, method=STAIR1, tol=1e-12, eps=0.0, maxit=100000, check_every=1,
+              history=True):
+        """Iterate Eq. (2) from x0 (default uniform 1/N) until resid <= tol,
+        step <= eps or maxit.  Returns dict(x, sweeps, resid, step, hist)."""
+        x = np.full(self.N, 1.0 / self.N) if x0 is None else _c64(x0).reshape(-1).copy()
+        hist = np.zeros(maxit) if history else None
+        out = np.zeros(2)
+        k = _load().or_solve(self.L, self.m, int(method), _p(self.Tlo), _p(self.Tdd), _p(self.Tup),
+                             _p(self.LU), _p(self.piv), _p(x), float(tol), float(eps), int(maxit),
+                             int(check_every), _p(hist) if history else None, _p(out))
+        if k == -1:
+            raise FloatingPointError("breakdown: e^T z <= 0 or not finite")
+        return dict(x=x, sweeps=int(k), resid=float(out[0]), step=float(out[1]),
+                    hist=hist[:k] if history else None)
+
+    def iteration_matrix(self, method=STAIR1):
+        """Dense M^{-1} N, column k = unnormalised sweep of e_k (small N only)."""
+        assert self.N <= 4096
+        G = np.empty((self.N, self.N))
+        e = np.zeros(self.N)
+        for k in range(self.N):
+            e[:] = 0.0
+            e[k] = 1.0
+            G[:, k] = self.sweep(e, method)
+        return G
+
+    def dense_T(self):
+        """Dense T = Q^T (small N only)."""
+        L, m = self.L, self.m
+        T = np.zeros((self.N, self.N))
+        for l in range(L):
+            T[l * m:(l + 1) * m, l * m:(l + 1) * m] = self.Tdd[l]
+            if l > 0:
+                T[l * m:(l + 1) * m, (l - 1) * m:l * m] = self.Tlo[l]
+            if l < L - 1:
+                T[l * m:(l + 1) * m, (l + 1) * m:(l + 2) * m] = self.Tup[l]
+        return T
+
+
+def _seqsum(v):
+    s = 0.0
+    for t in v:
+        s += t
+    return s
+
+
+def contraction(err_hist, window=50):
+    """Observed contraction factor (d_k / d_{k-w})^(1/w) at the end of a run."""
+    d = np.asarray(err_hist)
+    w = min(window, len(d) - 1)
+    return float((d[-1] / d[-1 - w]) ** (1.0 / w))

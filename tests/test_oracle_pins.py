@@ -1,0 +1,291 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test would fail under a plausible mistake in the oracle: a swapped
+parity, a wrong index set in Algorithm 2, a transposed block, a dropped
+boundary term, a wrong sign or a wrong normalisation.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from conftest import read_golden
+
+
+def chain_from_T(A, m=1):
+    """Oracle chain whose T = Q^T equals the given block-tridiagonal A."""
+    N = A.shape[0]
+    L = N // m
+    Q = A.T
+    dn = np.zeros((L, m, m)); loc = np.zeros((L, m, m)); up = np.zeros((L, m, m))
+    for l in range(L):
+        s = slice(l * m, (l + 1) * m)
+        loc[l] = Q[s, s]
+        if l > 0:
+            dn[l] = Q[s, (l - 1) * m:l * m]
+        if l < L - 1:
+            up[l] = Q[s, (l + 1) * m:(l + 2) * m]
+    return oracle.Chain(dn, loc, up)
+
+
+def spectrum(G):
+    ev = np.linalg.eigvals(G)
+    return np.array(sorted(ev, key=lambda z: (round(z.real, 9), round(z.imag, 9))))
+
+
+def same_multiset(ev, ref, tol=1e-12):
+    ev = list(ev)
+    for r in ref:
+        k = int(np.argmin([abs(e - r) for e in ev]))
+        if abs(ev[k] - r) > tol:
+            return False
+        ev.pop(k)
+    return not ev
+
+
+# --- Sect. 2, Examples 1 and 2 -------------------------------------------------
+
+def test_example1_and_2_spectra():
+    g = read_golden("example1_2.txt")
+    A = np.array(g["matrix"])
+    ch = chain_from_T(A)
+    assert np.array_equal(ch.dense_T(), A)
+    assert same_multiset(np.linalg.eigvals(ch.iteration_matrix(oracle.BJ)), g["jacobi"][0])
+    assert same_multiset(np.linalg.eigvals(ch.iteration_matrix(oracle.BGS)), g["gauss_seidel"][0])
+    assert same_multiset(np.linalg.eigvals(ch.iteration_matrix(oracle.STAIR1)), g["stair1"][0])
+    # the transposed matrix has the same spectra (the paper's matrix has zero
+    # row sums, i.e. it is really Q; reading it as Q^T or Q gives one answer)
+    chT = chain_from_T(A.T.copy())
+    assert same_multiset(np.linalg.eigvals(chT.iteration_matrix(oracle.STAIR1)), g["stair1"][0])
+
+
+def test_example2_pins_index_set_reading():
+    """Algorithm 2 step 1 read literally (k = i included for coupled rows)
+    does NOT give Example 2's spectrum; the reading with k != i does."""
+    g = read_golden("example1_2.txt")
+    A = np.array(g["matrix"])
+    n = 4
+    # literal reading, 1-based rows: odd rows J={i}; even rows J={i-1,i+1}
+    G = np.zeros((n, n))
+    for c in range(n):
+        x = np.zeros(n); x[c] = 1.0
+        z = np.zeros(n)
+        for i in range(1, n + 1):
+            J = {i} if i % 2 == 1 else {i - 1, i + 1} & set(range(1, n + 1))
+            z[i - 1] = -sum(A[i - 1, k - 1] * x[k - 1] for k in range(1, n + 1) if k not in J)
+        for i in range(1, n + 1, 2):
+            z[i - 1] = z[i - 1] / A[i - 1, i - 1]
+        for i in range(2, n + 1, 2):
+            J = {i - 1, i + 1} & set(range(1, n + 1))
+            z[i - 1] = (z[i - 1] - sum(A[i - 1, k - 1] * z[k - 1] for k in J)) / A[i - 1, i - 1]
+        G[:, c] = z
+    assert not same_multiset(np.linalg.eigvals(G), g["stair1"][0], tol=1e-6)
+    ours = chain_from_T(A).iteration_matrix(oracle.STAIR1)
+    assert same_multiset(np.linalg.eigvals(ours), g["stair1"][0])
+
+
+# --- splittings against explicitly assembled M, N ----------------------------
+
+def stair_M(T, L, m, typ):
+    """Stair matrix of type 1 or 2 assembled from dense T (Sect. 2)."""
+    M = np.zeros_like(T)
+    for l in range(L):
+        s = slice(l * m, (l + 1) * m)
+        M[s, s] = T[s, s]
+        one_based_odd = (l + 1) % 2 == 1
+        coupled = (not one_based_odd) if typ == 1 else one_based_odd
+        if coupled:
+            if l > 0:
+                M[s, (l - 1) * m:l * m] = T[s, (l - 1) * m:l * m]
+            if l < L - 1:
+                M[s, (l + 1) * m:(l + 2) * m] = T[s, (l + 1) * m:(l + 2) * m]
+    return M
+
+
+def bgs_M(T, L, m):
+    M = np.zeros_like(T)
+    for l in range(L):
+        M[l * m:(l + 1) * m, :(l + 1) * m] = T[l * m:(l + 1) * m, :(l + 1) * m]
+    return M
+
+
+def bj_M(T, L, m):
+    M = np.zeros_like(T)
+    for l in range(L):
+        s = slice(l * m, (l + 1) * m)
+        M[s, s] = T[s, s]
+    return M
+
+
+def dense_QT(dn, loc, up):
+    """Q^T assembled straight from the generator blocks (independent of the oracle)."""
+    L, m, _ = loc.shape
+    Q = np.zeros((L * m, L * m))
+    for l in range(L):
+        Q[l * m:(l + 1) * m, l * m:(l + 1) * m] = loc[l]
+        if l > 0:
+            Q[l * m:(l + 1) * m, (l - 1) * m:l * m] = dn[l]
+        if l < L - 1:
+            Q[l * m:(l + 1) * m, (l + 1) * m:(l + 2) * m] = up[l]
+    return Q.T.copy()
+
+
+@pytest.mark.parametrize("L,m", [(7, 3), (8, 4), (2, 5), (3, 1), (9, 2)])
+def test_sweeps_equal_dense_splittings(L, m):
+    dn, loc, up = synth.qbd(L, m, 0.8, seed=21 + L, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    T = dense_QT(dn, loc, up)
+    assert np.allclose(ch.dense_T(), T, rtol=0, atol=0)
+    x = np.random.default_rng(L * 100 + m).random(L * m)
+    for meth, M in [(oracle.STAIR1, stair_M(T, L, m, 1)), (oracle.STAIR2, stair_M(T, L, m, 2)),
+                    (oracle.BGS, bgs_M(T, L, m)), (oracle.BJ, bj_M(T, L, m))]:
+        N = M - T
+        ref = np.linalg.solve(M, N @ x)
+        z = ch.sweep(x, meth)
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), meth
+
+
+def test_residual_against_dense():
+    dn, loc, up = synth.qbd(9, 4, 0.8, seed=4, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    x = np.random.default_rng(0).random(36)
+    ref = np.abs(dense_QT(dn, loc, up) @ x).sum()
+    assert abs(ch.residual(x) - ref) <= 1e-13 * ref
+
+
+# --- LU --------------------------------------------------------------------------
+
+def test_lu_reconstruction_no_swaps_on_diag_blocks():
+    dn, loc, up = synth.qbd(20, 16, 0.9, seed=9, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    assert ch.swaps == 0          # column-diagonally dominant blocks
+    for l in range(ch.L):
+        LU = ch.LU[l]
+        Lm = np.tril(LU, -1) + np.eye(ch.m)
+        Um = np.triu(LU)
+        err = np.abs(Lm @ Um - ch.Tdd[l]).max()
+        assert err <= 1e-14 * np.abs(ch.Tdd[l]).max() * ch.m
+
+
+def test_lu_partial_pivoting_general_matrix():
+    import ctypes
+    rng = np.random.default_rng(5)
+    m = 9
+    A = rng.standard_normal((m, m))
+    LU = A.copy()
+    piv = np.zeros(m, np.int32)
+    lib = oracle._load()
+    swaps = lib.or_lu(m, ctypes.c_void_p(LU.ctypes.data), ctypes.c_void_p(piv.ctypes.data))
+    assert swaps > 0
+    P = np.eye(m)
+    for k in range(m):
+        P[[k, piv[k]]] = P[[piv[k], k]]
+    Lm = np.tril(LU, -1) + np.eye(m)
+    assert np.abs(P @ A - Lm @ np.triu(LU)).max() < 1e-13
+    assert np.abs(np.tril(LU, -1)).max() <= 1.0 + 1e-15      # |l_ik| <= 1
+    b = rng.standard_normal(m)
+    x = b.copy()
+    lib.or_lu_solve(m, ctypes.c_void_p(LU.ctypes.data), ctypes.c_void_p(piv.ctypes.data),
+                    ctypes.c_void_p(x.ctypes.data))
+    assert np.abs(A @ x - b).max() < 1e-12
+    Z = np.zeros((m, m)); Z[:, 0] = 1.0
+    assert lib.or_lu(m, ctypes.c_void_p(Z.ctypes.data), ctypes.c_void_p(piv.ctypes.data)) == -1
+
+
+# --- the limit pi ------------------------------------------------------------------
+
+def direct_pi(dn, loc, up):
+    """Dense direct solve of Q^T pi = 0 with one equation replaced by e^T pi = 1."""
+    T = dense_QT(dn, loc, up)
+    T[-1, :] = 1.0
+    b = np.zeros(T.shape[0]); b[-1] = 1.0
+    return np.linalg.solve(T, b)
+
+
+@pytest.mark.parametrize("L,m,dep", [(6, 3, True), (11, 4, True), (64, 8, False), (5, 1, True)])
+def test_limit_matches_dense_direct_solve(L, m, dep):
+    dn, loc, up = synth.qbd(L, m, 0.8, seed=L + m, level_dependent=dep)
+    ch = oracle.Chain(dn, loc, up)
+    res = ch.solve(tol=1e-14, maxit=200000, check_every=10)
+    pi = res["x"]
+    ref = direct_pi(dn, loc, up)
+    assert np.abs(pi - ref).sum() / np.abs(ref).sum() <= 1e-11
+    assert (pi >= 0).all() and abs(pi.sum() - 1.0) <= 1e-14
+    assert res["resid"] <= 1e-14
+
+
+def test_birth_death_closed_form():
+    L, lam, mu = 64, 0.8, 1.0
+    ch = oracle.Chain(*synth.birth_death(L, lam, mu))
+    res = ch.solve(tol=1e-15, maxit=100000, check_every=10)
+    r = lam / mu
+    ref = (1 - r) * r ** np.arange(L) / (1 - r ** L)
+    assert np.abs(res["x"] - ref).sum() / ref.sum() <= 1e-11
+    # the residual of the exact closed form is at the rounding floor
+    assert ch.residual(ref) <= 1e-15
+
+
+def test_stopping_rule_step_error():
+    dn, loc, up = synth.qbd(16, 4, 0.8, seed=1, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    res = ch.solve(tol=0.0, eps=1e-9, maxit=100000)
+    h = res["hist"]
+    assert h[-1] <= 1e-9 < h[-2]
+    res2 = ch.solve(tol=0.0, eps=0.0, maxit=37)
+    assert res2["sweeps"] == 37
+
+
+def test_breakdown_detected():
+    dn, loc, up = synth.qbd(6, 2, 0.8, seed=1, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    with pytest.raises(FloatingPointError):
+        ch.solve(x0=-np.ones(12) / 12, maxit=5)
+
+
+# --- convergence rate (Sect. 2, feature 2) ------------------------------------------
+
+def second_eig(G):
+    ev = np.linalg.eigvals(G)
+    ev = ev[np.argsort(-np.abs(ev))]
+    assert abs(ev[0] - 1.0) < 1e-10
+    return abs(ev[1])
+
+
+@pytest.mark.parametrize("L,m,seed", [(8, 3, 1), (10, 4, 2), (7, 5, 3)])
+def test_stair_bgs_same_spectrum_and_young(L, m, seed):
+    dn, loc, up = synth.qbd(L, m, 0.8, seed=seed, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    G1 = ch.iteration_matrix(oracle.STAIR1)
+    G2 = ch.iteration_matrix(oracle.STAIR2)
+    Gg = ch.iteration_matrix(oracle.BGS)
+    Gj = ch.iteration_matrix(oracle.BJ)
+    # eigenvalues near 0 sit in Jordan blocks and are ill-conditioned; the
+    # well-separated part of the spectrum (|lambda| > 0.05) must coincide
+    def big(G):
+        e = np.sort(np.abs(np.linalg.eigvals(G)))
+        return e[e > 0.05]
+    e1, e2, eg = big(G1), big(G2), big(Gg)
+    assert len(e1) == len(eg) == len(e2) and len(eg) >= L // 2
+    assert np.abs(e1 - eg).max() <= 1e-9 and np.abs(e2 - eg).max() <= 1e-9
+    ej = np.linalg.eigvals(Gj)
+    # block Jacobi on a bipartite level graph: -1 is an eigenvalue too
+    assert np.min(np.abs(ej + 1.0)) < 1e-9
+    gj = np.sort(np.abs(ej))[-3]           # largest modulus other than +-1
+    assert abs(second_eig(Gg) - gj ** 2) <= 1e-9
+
+
+@pytest.mark.slow
+def test_observed_contraction_equals_bgs_and_eigenvalue():
+    dn, loc, up = synth.workload("qbd_L64_m8")
+    ch = oracle.Chain(dn, loc, up)
+    gamma = second_eig(ch.iteration_matrix(oracle.STAIR1))
+    r1 = ch.solve(tol=0.0, eps=1e-14, maxit=20000)
+    rg = ch.solve(tol=0.0, eps=1e-14, maxit=20000, method=oracle.BGS)
+    # asymptotic regime: a window before the rounding floor
+    k1 = oracle.contraction(r1["hist"][: int(0.8 * len(r1["hist"]))], 200)
+    kg = oracle.contraction(rg["hist"][: int(0.8 * len(rg["hist"]))], 200)
+    assert abs(k1 - kg) < 1e-3
+    assert abs(k1 - gamma) < 1e-3
+    # block Jacobi does not converge (|lambda| = 1 twice)
+    rj = ch.solve(tol=0.0, eps=1e-14, maxit=400, method=oracle.BJ)
+    assert rj["sweeps"] == 400 and rj["step"] > 1e-6
