@@ -1,0 +1,215 @@
+/*
+ * mc.h -- C ABI of libmc: the block staircase stationary iteration for the
+ * stationary vector of a Markov chain on one NVIDIA GB300 (sm_103a).
+ *
+ * Method (Besozzi, Della Bartola, Gemignani, arXiv 2302.07551):
+ *   Eq. (1)      find pi with Q^T pi = 0, pi >= 0, e^T pi = 1 for an
+ *                irreducible generator Q;
+ *   Sect. 2      regular splitting Q^T = M - N with M a stair matrix;
+ *   Eq. (2)      M x_{k+1} = N x_k, then x_{k+1} <- x_{k+1} / e^T x_{k+1};
+ *   Algorithm 2  one sweep in two data-parallel steps over block rows;
+ *   Sect. 3      stopping rule ||x_k - x_{k+1}||_1 <= eps or k >= maxit.
+ *
+ * Scope: block-tridiagonal Q^T (QBD-like generators) with L levels of m
+ * phases each, N = L*m.  Level l (0-based) is block row l+1 of the paper.
+ *
+ * Conventions for every entry point
+ *   - Device pointers are CUDA device addresses on the current device; all
+ *     work is enqueued on the stream given to mc_create (NULL = legacy
+ *     default stream).  Entry points marked "async" return before the GPU
+ *     finishes; entry points marked "syncs" block on that stream.
+ *   - The library never allocates device memory: the caller passes one
+ *     workspace of at least mc_workspace_bytes() bytes, 256-byte aligned,
+ *     which must outlive the handle.  The handle itself is host memory owned
+ *     by the library (free it with mc_destroy).
+ *   - Every call returns an mc_status; none aborts, traps or hangs.  Host
+ *     side argument errors are reported before any GPU work.  Errors found
+ *     on the device are latched into a status word in the workspace and are
+ *     returned by the next syncing call (mc_factor, mc_solve, mc_residual,
+ *     mc_sweep_host, mc_sync), which also clears the latch.
+ *   - A handle may be used by one host thread at a time.
+ */
+#ifndef MC_H
+#define MC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  MC_OK = 0,
+  MC_ERR_ARG = 1,             /* invalid argument (checked on the host)        */
+  MC_ERR_WORKSPACE = 2,       /* workspace NULL, misaligned or too small       */
+  MC_ERR_CUDA = 3,            /* a CUDA runtime call failed                    */
+  MC_ERR_SINGULAR_BLOCK = 4,  /* a diagonal block has a zero/non-finite pivot  */
+  MC_ERR_NOT_FACTORED = 5,    /* sweep/solve before a successful mc_factor     */
+  MC_ERR_BREAKDOWN = 6,       /* e^T z <= 0 or not finite during normalisation */
+  MC_ERR_NO_CONVERGENCE = 7,  /* mc_solve reached maxit                        */
+  MC_ERR_TIMEOUT = 8          /* a bounded device-side wait gave up            */
+} mc_status;
+
+/* Storage type of the blocks streamed by the sweep.  This version: MC_F64. */
+typedef enum { MC_F64 = 0 } mc_dtype;
+
+/*
+ * How the diagonal-block solves Q_{i,i}^{-1} of Algorithm 2 (steps 2 and 3)
+ * are applied.  Both are computed from the LU factors of mc_factor and give
+ * the same iterates up to rounding.
+ *   MC_APPLY_INVERSE: store (-Q_{i,i})^{-1} (entrywise >= 0, Q^T being a
+ *     singular M-matrix up to sign) and apply it as a dense product after
+ *     the neighbour products: 3 m^2 FP64 multiply-adds and 24 m^2 bytes per
+ *     level and sweep.
+ *   MC_APPLY_COUPLED: store W_lo = (-Q_{i,i})^{-1} Q_{i,i-1} and
+ *     W_up = (-Q_{i,i})^{-1} Q_{i,i+1} (both >= 0), so that each level is
+ *     one product z_i = W_lo v_{i-1} + W_up v_{i+1}: 2 m^2 multiply-adds
+ *     and 16 m^2 bytes per level and sweep.
+ */
+typedef enum { MC_APPLY_INVERSE = 0, MC_APPLY_COUPLED = 1 } mc_apply;
+
+/* Planes of stored blocks, for mc_export. */
+typedef enum {
+  MC_PLANE_TLO = 0,   /* Q^T block (l, l-1)  = (Q_{l-1,l})^T; zero at l = 0     */
+  MC_PLANE_TUP = 1,   /* Q^T block (l, l+1)  = (Q_{l+1,l})^T; zero at l = L-1   */
+  MC_PLANE_TDD = 2,   /* Q^T block (l, l)    = (Q_{l,l})^T                      */
+  MC_PLANE_LU = 3,    /* LU of TDD: unit L strictly below, U on/above diagonal  */
+  MC_PLANE_NINV = 4,  /* (-TDD)^{-1}                                           */
+  MC_PLANE_WLO = 5,   /* (-TDD)^{-1} TLO   (MC_APPLY_COUPLED only)                */
+  MC_PLANE_WUP = 6    /* (-TDD)^{-1} TUP   (MC_APPLY_COUPLED only)                */
+} mc_plane;
+
+typedef struct {
+  int64_t L;       /* number of levels (block rows), L >= 2                     */
+  int32_t m;       /* phases per level (block size), 1 <= m <= 256              */
+  int32_t stair;   /* 1: stair matrix of type 1 (default), 2: type 2 (Sect. 2)  */
+  int32_t apply;   /* mc_apply                                                  */
+  int32_t dtype;   /* mc_dtype; must be MC_F64                                  */
+} mc_desc;
+
+typedef struct {
+  int64_t sweeps;       /* sweeps performed                                    */
+  double residual_l1;   /* ||Q^T pi||_1 of the returned pi (direct, FP64)      */
+  double step_l1;       /* ||x_k - x_{k-1}||_1 of the last sweep (Sect. 3)     */
+  double contraction;   /* (step_k / step_{k-c})^(1/c) over the last check     */
+  int32_t converged;    /* 1 if a stopping test other than maxit fired         */
+} mc_result;
+
+typedef struct mc_chain mc_chain;
+
+/* Bytes of device workspace needed for desc (0 if desc is invalid). */
+size_t mc_workspace_bytes(const mc_desc* desc);
+
+/*
+ * Create a chain from the generator blocks of Q (Eq. (1); the blocks Q_{i,j}
+ * of Sect. 2 are the blocks of Q^T, formed here by transposition).
+ *   dn, loc, up: device pointers to L blocks each of m x m doubles, row-major,
+ *     contiguous ([L][m][m]): dn[l] = Q_{l,l-1}, loc[l] = Q_{l,l} (diagonal
+ *     included), up[l] = Q_{l,l+1}.  dn[0] and up[L-1] are ignored.  8-byte
+ *     aligned.  They are copied into the workspace during this call's stream
+ *     work and may be freed once that work has completed.
+ *   workspace, ws_bytes: caller-owned device memory (see conventions).
+ *   cuda_stream: cudaStream_t on which all work of this handle is enqueued.
+ *   out: receives the handle.
+ * Async.  Errors: MC_ERR_ARG (bad desc, NULL pointers, misaligned blocks),
+ * MC_ERR_WORKSPACE, MC_ERR_CUDA.
+ */
+int mc_create(const mc_desc* desc, const double* dn, const double* loc, const double* up,
+              void* workspace, size_t ws_bytes, void* cuda_stream, mc_chain** out);
+
+/*
+ * Factor the diagonal blocks Q_{i,i} (as blocks of Q^T) by batched LU without
+ * pivoting (the blocks of a generator's transpose are strictly diagonally
+ * dominant by columns, so no row exchange is ever needed) and form the
+ * operators that apply Q_{i,i}^{-1} in Algorithm 2 steps 2 and 3 (see
+ * mc_apply).  Syncs once.  Errors: MC_ERR_SINGULAR_BLOCK if a pivot is zero
+ * or not finite (the handle stays unfactored), MC_ERR_CUDA.
+ */
+int mc_factor(mc_chain* chain);
+
+/*
+ * nsweeps sweeps of Eq. (2) with M the stair matrix of desc.stair, each as in
+ * Algorithm 2: for the diagonal-only block rows (0-based even levels for
+ * type 1) z_l = Q_{l,l}^{-1}(-Q_{l,l-1} x_{l-1} - Q_{l,l+1} x_{l+1}); then for
+ * the coupled rows z_l = Q_{l,l}^{-1}(-Q_{l,l-1} z_{l-1} - Q_{l,l+1} z_{l+1});
+ * then x <- z / e^T z and step = ||x_new - x_old||_1.
+ *   x_in, x_out: device vectors of N doubles (x_in is not modified unless it
+ *     equals x_out; in-place is allowed).  x_in should satisfy e^T x_in = 1
+ *     for step to be the paper's step error.
+ *   nsweeps >= 1.
+ *   stats_dev: NULL or device array of 3 doubles receiving, for the last
+ *     sweep, [e^T z, ||x_new - x_old||_1, NaN] (the third slot is reserved).
+ * Async.  Errors: MC_ERR_ARG, MC_ERR_NOT_FACTORED, MC_ERR_CUDA; a breakdown
+ * (e^T z <= 0 or not finite) is latched on the device (MC_ERR_BREAKDOWN).
+ */
+int mc_sweep(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps,
+             double* stats_dev);
+
+/*
+ * As mc_sweep but with HOST vectors (pinned memory recommended): copies
+ * x_in_host to the device, sweeps, copies the result to x_out_host and
+ * stats (3 doubles, may be NULL) to stats_host.  Syncs.
+ */
+int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, int64_t nsweeps,
+                  double* stats_host);
+
+/*
+ * Diagnostics: exactly mc_sweep(x_in, x_out, nsweeps, NULL), with CUDA events
+ * recorded on the handle's stream around each of the three kernel launches
+ * of every sweep.  ms_host (4 doubles, host) receives the summed device time
+ * in milliseconds of half-sweep 1, half-sweep 2 and the normalisation, and
+ * the number of kernel launches.  1 <= nsweeps <= 2^20.  Syncs.
+ */
+int mc_profile(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps,
+               double* ms_host);
+
+/*
+ * Solve Eq. (1) by iterating Eq. (2) (Algorithm 2 loop).
+ *   x0: NULL (start from the uniform vector 1/N) or a device vector of N
+ *     doubles, entries >= 0 with positive sum (normalised on entry).
+ *   pi: device output, N doubles.
+ *   tol: stop when ||Q^T pi||_1 <= tol (direct FP64 residual, evaluated every
+ *     check_every sweeps and at maxit); tol <= 0 disables.
+ *   eps: stop when the step error of Sect. 3 is <= eps (evaluated every
+ *     check_every sweeps); eps <= 0 disables.
+ *   maxit: sweep limit (>= 1).  check_every >= 1: sweeps per check; the
+ *     sweeps between checks run as one CUDA graph.
+ *   res: receives the result (may be NULL).
+ * Syncs once per check.  Errors: MC_ERR_ARG (bad sizes, x0 with a negative
+ * entry or zero sum), MC_ERR_NOT_FACTORED, MC_ERR_BREAKDOWN,
+ * MC_ERR_NO_CONVERGENCE (maxit reached with tol or eps enabled; pi and res
+ * still hold the last iterate), MC_ERR_CUDA.
+ */
+int mc_solve(mc_chain* chain, const double* x0, double* pi, double tol, double eps, int64_t maxit,
+             int32_t check_every, mc_result* res);
+
+/*
+ * ||Q^T pi||_1 (Eq. (1)) computed directly from the stored FP64 blocks.
+ *   pi: device vector of N doubles.  resid_l1_host: host output.
+ * Syncs.  Errors: MC_ERR_ARG, MC_ERR_CUDA.
+ */
+int mc_residual(mc_chain* chain, const double* pi, double* resid_l1_host);
+
+/*
+ * Copy count stored blocks of a plane, levels [level0, level0+count), to
+ * dst_dev as count packed m x m blocks in COLUMN-major order (entry (i, j) of
+ * a block of Q^T at j*m + i).  Async.  Errors: MC_ERR_ARG (range, plane not
+ * stored for this desc.apply, LU/NINV/W* before mc_factor), MC_ERR_CUDA.
+ */
+int mc_export(mc_chain* chain, int32_t plane, int64_t level0, int64_t count, double* dst_dev);
+
+/* Wait for the handle's stream and return (and clear) the device status. */
+int mc_sync(mc_chain* chain);
+
+/* Release the handle (host memory only; the workspace stays the caller's). */
+void mc_destroy(mc_chain* chain);
+
+/* Static description of a status code. */
+const char* mc_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MC_H */

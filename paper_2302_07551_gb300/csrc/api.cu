@@ -1,0 +1,456 @@
+// Host side of the libmc C ABI (declarations and contracts in include/mc.h).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "mc_internal.cuh"
+
+struct mc_chain {
+  mc_desc d;
+  mc::Layout lay;
+  char* ws;
+  cudaStream_t user;         // caller's stream: every enqueue goes here
+  cudaStream_t cap;          // private stream used only to capture graphs
+  int num_sms;
+  int factored;
+  int nb_phase, nw;          // persistent sweep grid (blocks, warps)
+  int nb_norm, nb_resid;
+  mc::Header* hdr;           // device header inside the workspace
+  mc::Header* hh;            // pinned host copy of the header
+  double *planes, *z, *xa, *xb, *wpart, *dpart, *rpart;
+  cudaGraphExec_t gexec;     // cached chunk graph of mc_solve
+  int g_chunk, g_resid;
+};
+
+namespace mc {
+
+static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static bool desc_ok(const mc_desc* d) {
+  return d && d->L >= 2 && d->L <= (int64_t)1 << 31 && d->m >= 1 && d->m <= kMaxM &&
+         (d->stair == 1 || d->stair == 2) &&
+         (d->apply == MC_APPLY_INVERSE || d->apply == MC_APPLY_COUPLED) && d->dtype == MC_F64;
+}
+
+Layout make_layout(const mc_desc& d) {
+  Layout y{};
+  y.L = d.L;
+  y.m = d.m;
+  y.N = d.L * d.m;
+  y.ms = (int)round_up((size_t)d.m * d.m, 32);
+  y.n_planes = d.apply == MC_APPLY_COUPLED ? 7 : 5;
+  y.plane_bytes = (size_t)d.L * y.ms * sizeof(double);
+  y.vec_bytes = round_up((size_t)y.N, 32) * sizeof(double);
+  size_t o = 0;
+  y.off_hdr = o;
+  o += 4096;
+  y.off_planes = o;
+  o += y.plane_bytes * y.n_planes;
+  y.off_z = o;
+  o += y.vec_bytes;
+  y.off_xa = o;
+  o += y.vec_bytes;
+  y.off_xb = o;
+  o += y.vec_bytes;
+  y.off_wpart = o;
+  o += round_up(2 * kMaxWarps * sizeof(double), 256);
+  y.off_dpart = o;
+  o += round_up(kMaxNormBlocks * sizeof(double), 256);
+  y.off_rpart = o;
+  o += round_up(kMaxWarps * sizeof(double), 256);
+  y.total = o;
+  return y;
+}
+
+}  // namespace mc
+
+using namespace mc;
+
+#define CK(call)                                   \
+  do {                                             \
+    if ((call) != cudaSuccess) return MC_ERR_CUDA; \
+  } while (0)
+
+// Enqueue one sweep.  ev (optional) = 4 events recorded before half-sweep 1,
+// between the half-sweeps, before and after the normalisation.
+static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* stats_out,
+                         cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const int64_t L = c->lay.L;
+  const int p1 = c->d.stair == 1 ? 0 : 1;   // 0-based parity of the diagonal-only rows
+  const int p2 = 1 - p1;
+  const bool coupled = c->d.apply == MC_APPLY_COUPLED;
+  const size_t pe = c->lay.plane_bytes / sizeof(double);
+  PhaseArgs a{};
+  a.A = c->planes + (coupled ? kPlaneWLO : kPlaneTLO) * pe;
+  a.B = c->planes + (coupled ? kPlaneWUP : kPlaneTUP) * pe;
+  a.C = c->planes + kPlaneNINV * pe;
+  a.L = L;
+  a.m = c->lay.m;
+  a.ms = c->lay.ms;
+  // half-sweep 1: diagonal-only rows read x at their neighbours
+  a.src = src;
+  a.dst = c->z;
+  a.wpart = c->wpart;
+  a.parity = p1;
+  a.P = (L - p1 + 1) / 2;
+  if (ev) CK(cudaEventRecord(ev[0], s));
+  CK(launch_phase(a, coupled, c->nb_phase, s));
+  if (ev) CK(cudaEventRecord(ev[1], s));
+  // half-sweep 2: coupled rows read the fresh z of their neighbours
+  a.src = c->z;
+  a.wpart = c->wpart + c->nw;
+  a.parity = p2;
+  a.P = (L - p2 + 1) / 2;
+  CK(launch_phase(a, coupled, c->nb_phase, s));
+  if (ev) CK(cudaEventRecord(ev[2], s));
+  NormArgs n{};
+  n.z = c->z;
+  n.x_old = src;
+  n.x_new = dst;
+  n.wpart = c->wpart;
+  n.dpart = c->dpart;
+  n.hdr = c->hdr;
+  n.stats_out = stats_out;
+  n.N = c->lay.N;
+  n.n_wpart = 2 * c->nw;
+  CK(launch_normalise(n, c->nb_norm, s));
+  if (ev) CK(cudaEventRecord(ev[3], s));
+  return MC_OK;
+}
+
+static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s) {
+  const size_t pe = c->lay.plane_bytes / sizeof(double);
+  ResidArgs r{};
+  r.TLO = c->planes + kPlaneTLO * pe;
+  r.TDD = c->planes + kPlaneTDD * pe;
+  r.TUP = c->planes + kPlaneTUP * pe;
+  r.x = x;
+  r.rpart = c->rpart;
+  r.hdr = c->hdr;
+  r.out = nullptr;
+  r.L = c->lay.L;
+  r.m = c->lay.m;
+  r.ms = c->lay.ms;
+  CK(launch_residual(r, c->nb_resid, s));
+  return MC_OK;
+}
+
+// Wait for the stream, fetch the header, clear a latched status.
+static int sync_header(mc_chain* c) {
+  CK(cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->user));
+  CK(cudaStreamSynchronize(c->user));
+  const int st = c->hh->status;
+  if (st != 0) {
+    CK(cudaMemsetAsync(&c->hdr->status, 0, sizeof(int32_t), c->user));
+    CK(cudaStreamSynchronize(c->user));
+  }
+  return st;
+}
+
+extern "C" {
+
+size_t mc_workspace_bytes(const mc_desc* desc) {
+  if (!desc_ok(desc)) return 0;
+  return make_layout(*desc).total;
+}
+
+int mc_create(const mc_desc* desc, const double* dn, const double* loc, const double* up,
+              void* workspace, size_t ws_bytes, void* cuda_stream, mc_chain** out) {
+  if (!out) return MC_ERR_ARG;
+  *out = nullptr;
+  if (!desc_ok(desc) || !dn || !loc || !up) return MC_ERR_ARG;
+  if (((uintptr_t)dn | (uintptr_t)loc | (uintptr_t)up) & 7u) return MC_ERR_ARG;
+  const Layout lay = make_layout(*desc);
+  if (!workspace || ((uintptr_t)workspace & 255u) || ws_bytes < lay.total) return MC_ERR_WORKSPACE;
+  int dev = 0;
+  CK(cudaGetDevice(&dev));
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  mc_chain* c = new (std::nothrow) mc_chain();
+  if (!c) return MC_ERR_ARG;
+  c->d = *desc;
+  c->lay = lay;
+  c->ws = (char*)workspace;
+  c->user = (cudaStream_t)cuda_stream;
+  c->num_sms = sms;
+  c->hdr = (Header*)(c->ws + lay.off_hdr);
+  c->planes = (double*)(c->ws + lay.off_planes);
+  c->z = (double*)(c->ws + lay.off_z);
+  c->xa = (double*)(c->ws + lay.off_xa);
+  c->xb = (double*)(c->ws + lay.off_xb);
+  c->wpart = (double*)(c->ws + lay.off_wpart);
+  c->dpart = (double*)(c->ws + lay.off_dpart);
+  c->rpart = (double*)(c->ws + lay.off_rpart);
+  // persistent grids: up to 16 warps per SM, never more warps than levels
+  const int64_t pmax = (lay.L + 1) / 2;
+  int64_t w = 16LL * sms;
+  if (w > pmax) w = pmax;
+  if (w > kMaxWarps) w = kMaxWarps;
+  c->nb_phase = (int)((w + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  c->nw = c->nb_phase * kWarpsPerBlock;
+  int64_t wr = 16LL * sms;
+  if (wr > lay.L) wr = lay.L;
+  if (wr > kMaxWarps) wr = kMaxWarps;
+  c->nb_resid = (int)((wr + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  int64_t nbn = (lay.N + 4 * kNormThreads - 1) / (4 * kNormThreads);
+  if (nbn > 2 * sms) nbn = 2 * sms;
+  if (nbn > kMaxNormBlocks) nbn = kMaxNormBlocks;
+  c->nb_norm = (int)(nbn < 1 ? 1 : nbn);
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {
+    delete c;
+    return MC_ERR_CUDA;
+  }
+  if (cudaHostAlloc((void**)&c->hh, sizeof(Header), cudaHostAllocDefault) != cudaSuccess) {
+    cudaStreamDestroy(c->cap);
+    delete c;
+    return MC_ERR_CUDA;
+  }
+  memset(c->hh, 0, sizeof(Header));
+  int rc = MC_OK;
+  if (cudaMemsetAsync(c->ws + lay.off_hdr, 0, 4096, c->user) != cudaSuccess ||
+      launch_layout(dn, loc, up, c->planes, lay, c->hdr, c->user) != cudaSuccess)
+    rc = MC_ERR_CUDA;
+  if (rc != MC_OK) {
+    mc_destroy(c);
+    return rc;
+  }
+  *out = c;
+  return MC_OK;
+}
+
+int mc_factor(mc_chain* c) {
+  if (!c) return MC_ERR_ARG;
+  c->factored = 0;
+  CK(launch_factor(c->planes, c->lay, c->hdr, c->d.apply == MC_APPLY_COUPLED, c->num_sms,
+                   c->user));
+  const int st = sync_header(c);
+  if (st != MC_OK) return st;
+  c->factored = 1;
+  return MC_OK;
+}
+
+int mc_sweep(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, double* stats_dev) {
+  if (!c || !x_in || !x_out || nsweeps < 1) return MC_ERR_ARG;
+  if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
+  if (!c->factored) return MC_ERR_NOT_FACTORED;
+  for (int64_t k = 0; k < nsweeps; ++k) {
+    const int rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out,
+                                 k == nsweeps - 1 ? stats_dev : nullptr, c->user);
+    if (rc != MC_OK) return rc;
+  }
+  return MC_OK;
+}
+
+int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, double* ms_host) {
+  if (!c || !x_in || !x_out || !ms_host || nsweeps < 1 || nsweeps > (1 << 20)) return MC_ERR_ARG;
+  if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
+  if (!c->factored) return MC_ERR_NOT_FACTORED;
+  const size_t ne = 4 * (size_t)nsweeps;
+  cudaEvent_t* ev = (cudaEvent_t*)calloc(ne, sizeof(cudaEvent_t));
+  if (!ev) return MC_ERR_ARG;
+  int rc = MC_OK;
+  size_t made = 0;
+  for (; made < ne; ++made)
+    if (cudaEventCreate(&ev[made]) != cudaSuccess) { rc = MC_ERR_CUDA; break; }
+  for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
+    rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out, nullptr, c->user, ev + 4 * k);
+  double t[3] = {0.0, 0.0, 0.0};
+  if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+  for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
+    for (int q = 0; q < 3; ++q) {
+      float ms = 0.0f;
+      if (cudaEventElapsedTime(&ms, ev[4 * k + q], ev[4 * k + q + 1]) != cudaSuccess) {
+        rc = MC_ERR_CUDA;
+        break;
+      }
+      t[q] += ms;
+    }
+  for (size_t i = 0; i < made; ++i) cudaEventDestroy(ev[i]);
+  free(ev);
+  if (rc != MC_OK) return rc;
+  ms_host[0] = t[0];
+  ms_host[1] = t[1];
+  ms_host[2] = t[2];
+  ms_host[3] = 3.0 * (double)nsweeps;
+  return sync_header(c);
+}
+
+int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int64_t nsweeps,
+                  double* stats_host) {
+  if (!c || !x_in_host || !x_out_host || nsweeps < 1) return MC_ERR_ARG;
+  if (!c->factored) return MC_ERR_NOT_FACTORED;
+  const size_t bytes = (size_t)c->lay.N * sizeof(double);
+  CK(cudaMemcpyAsync(c->xa, x_in_host, bytes, cudaMemcpyHostToDevice, c->user));
+  for (int64_t k = 0; k < nsweeps; ++k) {
+    const int rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->user);
+    if (rc != MC_OK) return rc;
+  }
+  CK(cudaMemcpyAsync(x_out_host, c->xa, bytes, cudaMemcpyDeviceToHost, c->user));
+  const int st = sync_header(c);
+  if (stats_host) {
+    stats_host[0] = c->hh->stats[0];
+    stats_host[1] = c->hh->stats[1];
+    stats_host[2] = nan("");
+  }
+  return st;
+}
+
+static int capture_chunk(mc_chain* c, int chunk, int with_resid) {
+  if (c->gexec) {
+    cudaGraphExecDestroy(c->gexec);
+    c->gexec = nullptr;
+  }
+  CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+  int rc = MC_OK;
+  for (int k = 0; k < chunk && rc == MC_OK; ++k) rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->cap);
+  if (rc == MC_OK && with_resid) rc = enqueue_residual(c, c->xa, c->cap);
+  if (rc == MC_OK &&
+      cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->cap) != cudaSuccess)
+    rc = MC_ERR_CUDA;
+  cudaGraph_t g = nullptr;
+  const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+  if (rc != MC_OK || e != cudaSuccess) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return MC_ERR_CUDA;
+  }
+  const cudaError_t e2 = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e2 != cudaSuccess) {
+    c->gexec = nullptr;
+    return MC_ERR_CUDA;
+  }
+  c->g_chunk = chunk;
+  c->g_resid = with_resid;
+  return MC_OK;
+}
+
+int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, int64_t maxit,
+             int32_t check_every, mc_result* res) {
+  if (!c || !pi || maxit < 1 || check_every < 1) return MC_ERR_ARG;
+  if (((uintptr_t)pi | (uintptr_t)x0) & 7u) return MC_ERR_ARG;
+  if (!c->factored) return MC_ERR_NOT_FACTORED;
+  const int64_t N = c->lay.N;
+  if (x0) {
+    CK(launch_check_scale(x0, c->xa, N, c->hdr, c->dpart, c->user));
+  } else {
+    CK(launch_fill(c->xa, N, 1.0 / (double)N, c->user));
+  }
+  int st = sync_header(c);
+  if (st != MC_OK) return st;
+  const int with_resid = tol > 0.0;
+  int64_t k = 0;
+  double d = NAN, d_prev = NAN, r = NAN, kappa = NAN;
+  int converged = 0;
+  while (k < maxit) {
+    const int64_t chunk = (maxit - k < check_every) ? (maxit - k) : check_every;
+    if (chunk == check_every) {
+      if (!c->gexec || c->g_chunk != check_every || c->g_resid != with_resid) {
+        const int rc = capture_chunk(c, check_every, with_resid);
+        if (rc != MC_OK) return rc;
+      }
+      CK(cudaGraphLaunch(c->gexec, c->user));
+      CK(cudaStreamSynchronize(c->user));
+    } else {
+      for (int64_t q = 0; q < chunk; ++q) {
+        const int rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->user);
+        if (rc != MC_OK) return rc;
+      }
+      if (with_resid) {
+        const int rc = enqueue_residual(c, c->xa, c->user);
+        if (rc != MC_OK) return rc;
+      }
+      CK(cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->user));
+      CK(cudaStreamSynchronize(c->user));
+    }
+    k += chunk;
+    st = c->hh->status;
+    if (st != 0) {
+      CK(cudaMemsetAsync(&c->hdr->status, 0, sizeof(int32_t), c->user));
+      CK(cudaStreamSynchronize(c->user));
+      return st;
+    }
+    d = c->hh->stats[1];
+    if (with_resid) r = c->hh->stats[2];
+    if (d_prev > 0.0 && d > 0.0) kappa = pow(d / d_prev, 1.0 / (double)chunk);
+    d_prev = d;
+    if ((with_resid && r <= tol) || (eps > 0.0 && d <= eps)) {
+      converged = 1;
+      break;
+    }
+  }
+  CK(cudaMemcpyAsync(pi, c->xa, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->user));
+  if (!with_resid) {
+    const int rc = enqueue_residual(c, c->xa, c->user);
+    if (rc != MC_OK) return rc;
+    st = sync_header(c);
+    if (st != MC_OK) return st;
+    r = c->hh->stats[2];
+  } else {
+    CK(cudaStreamSynchronize(c->user));
+  }
+  if (res) {
+    res->sweeps = k;
+    res->residual_l1 = r;
+    res->step_l1 = d;
+    res->contraction = kappa;
+    res->converged = converged;
+  }
+  if (!converged && (tol > 0.0 || eps > 0.0)) return MC_ERR_NO_CONVERGENCE;
+  return MC_OK;
+}
+
+int mc_residual(mc_chain* c, const double* pi, double* resid_l1_host) {
+  if (!c || !pi || !resid_l1_host || ((uintptr_t)pi & 7u)) return MC_ERR_ARG;
+  const int rc = enqueue_residual(c, pi, c->user);
+  if (rc != MC_OK) return rc;
+  const int st = sync_header(c);
+  *resid_l1_host = c->hh->stats[2];
+  return st;
+}
+
+int mc_export(mc_chain* c, int32_t plane, int64_t level0, int64_t count, double* dst_dev) {
+  if (!c || !dst_dev || plane < 0 || plane >= c->lay.n_planes || level0 < 0 || count < 0 ||
+      level0 + count > c->lay.L)
+    return MC_ERR_ARG;
+  if (plane >= kPlaneLU && !c->factored) return MC_ERR_ARG;
+  if (count == 0) return MC_OK;
+  const size_t pe = c->lay.plane_bytes / sizeof(double);
+  const size_t mm = (size_t)c->lay.m * c->lay.m;
+  const double* src = c->planes + plane * pe + (size_t)level0 * c->lay.ms;
+  CK(cudaMemcpy2DAsync(dst_dev, mm * sizeof(double), src, (size_t)c->lay.ms * sizeof(double),
+                       mm * sizeof(double), (size_t)count, cudaMemcpyDeviceToDevice, c->user));
+  return MC_OK;
+}
+
+int mc_sync(mc_chain* c) {
+  if (!c) return MC_ERR_ARG;
+  return sync_header(c);
+}
+
+void mc_destroy(mc_chain* c) {
+  if (!c) return;
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  if (c->hh) cudaFreeHost(c->hh);
+  delete c;
+}
+
+const char* mc_status_string(int s) {
+  switch (s) {
+    case MC_OK: return "ok";
+    case MC_ERR_ARG: return "invalid argument";
+    case MC_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
+    case MC_ERR_CUDA: return "CUDA runtime error";
+    case MC_ERR_SINGULAR_BLOCK: return "diagonal block with zero or non-finite pivot";
+    case MC_ERR_NOT_FACTORED: return "chain not factored";
+    case MC_ERR_BREAKDOWN: return "normalisation breakdown (e^T z <= 0 or not finite)";
+    case MC_ERR_NO_CONVERGENCE: return "no convergence within maxit";
+    case MC_ERR_TIMEOUT: return "device-side wait timed out";
+    default: return "unknown status";
+  }
+}
+
+}  // extern "C"

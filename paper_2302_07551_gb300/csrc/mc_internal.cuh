@@ -1,0 +1,100 @@
+// Internal declarations shared by the libmc translation units.
+//
+// Workspace layout (all regions 256-byte aligned, offsets in bytes):
+//   [hdr]      Header: status latch, last-block tickets, stats.
+//   [planes]   n_planes planes; plane p holds L blocks, block l at
+//              p*plane_bytes + l*ms*8, each block m x m doubles COLUMN-major
+//              (entry (i, j) of the Q^T block at j*m + i), ms = m*m rounded up
+//              to 32 doubles.  Column-major Q^T blocks are row-major Q blocks,
+//              so the layout step is a plain copy.
+//   [vectors]  z (sweep output before normalisation), xa, xb (iterate ping-pong
+//              of mc_solve / mc_sweep), each N doubles rounded to 32.
+//   [partials] per-warp level-sum partials of the two half-sweeps, per-block
+//              step-error partials, per-warp residual partials.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mc.h"
+
+namespace mc {
+
+constexpr int kMaxM = 256;
+constexpr int kWarpsPerBlock = 8;          // sweep / residual kernels: 256 threads
+constexpr int kMaxWarps = 8192;            // bound on the persistent sweep grid
+constexpr int kMaxNormBlocks = 2048;
+constexpr int kNormThreads = 256;
+
+struct Header {
+  int32_t status;        // first device-side error (mc_status), 0 = none
+  uint32_t ticket[7];    // last-block-done counters (0 between launches)
+  double stats[4];       // [e^T z, step_l1, resid_l1, spare]
+};
+
+// Plane indices match mc_plane.
+constexpr int kPlaneTLO = 0, kPlaneTUP = 1, kPlaneTDD = 2, kPlaneLU = 3, kPlaneNINV = 4,
+              kPlaneWLO = 5, kPlaneWUP = 6;
+
+struct Layout {
+  int64_t L, N;
+  int m, ms;             // block size and padded block stride (doubles)
+  int n_planes;
+  size_t plane_bytes, vec_bytes;
+  size_t off_hdr, off_planes, off_z, off_xa, off_xb, off_wpart, off_dpart, off_rpart, total;
+};
+
+Layout make_layout(const mc_desc& d);
+
+// Arguments of one half-sweep (Algorithm 2, step 1+2 or step 3).
+struct PhaseArgs {
+  const double* A;       // first operator plane (TLO, or WLO when coupled)
+  const double* B;       // second operator plane (TUP, or WUP when coupled)
+  const double* C;       // NINV plane (inverse mode), unused when coupled
+  const double* src;     // vector read at neighbour levels l-1, l+1
+  double* dst;           // z, written at this half-sweep's levels
+  double* wpart;         // one level-sum partial per warp
+  int64_t L, P;          // levels, levels in this half-sweep
+  int m, ms;
+  int parity;            // level of unit u is 2u + parity
+};
+
+struct NormArgs {
+  const double* z;
+  const double* x_old;
+  double* x_new;
+  const double* wpart;   // 2 * n_warps partials of e^T z
+  double* dpart;         // one per block
+  Header* hdr;
+  double* stats_out;     // optional extra copy of [s, step, NaN]
+  int64_t N;
+  int n_wpart;
+};
+
+struct ResidArgs {
+  const double* TLO;
+  const double* TDD;
+  const double* TUP;
+  const double* x;
+  double* rpart;         // one per warp
+  Header* hdr;
+  double* out;           // optional copy of the residual (device)
+  int64_t L;
+  int m, ms;
+};
+
+// Launchers (return cudaGetLastError()).
+cudaError_t launch_layout(const double* dn, const double* loc, const double* up, double* planes,
+                          const Layout& lay, Header* hdr, cudaStream_t s);
+cudaError_t launch_factor(double* planes, const Layout& lay, Header* hdr, int coupled,
+                          int num_sms, cudaStream_t s);
+cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s);
+cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s);
+cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
+cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
+cudaError_t launch_check_scale(const double* x0, double* x, int64_t n, Header* hdr,
+                               double* dpart, cudaStream_t s);
+
+// Latch an error code into the header (first error wins).
+__device__ __forceinline__ void latch(Header* h, int code) { atomicCAS(&h->status, 0, code); }
+
+}  // namespace mc

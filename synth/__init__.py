@@ -30,6 +30,8 @@ WORKLOADS = {
     "birth_death_L64": dict(kind="birth_death", L=64, m=1, lam=0.8, mu=1.0),
     # L=32768, m=64, level-dependent, ratio 0.9 (FP64 blocks ~3.2 GB)
     "qbd_L32768_m64": dict(kind="qbd", L=32768, m=64, ratio=0.9, level_dependent=True, seed=1),
+    # same recipe at L=8192 (0.8 GB of blocks per sweep): profiling-size case
+    "qbd_L8192_m64": dict(kind="qbd", L=8192, m=64, ratio=0.9, level_dependent=True, seed=1),
     # jumps +-1, +-2 on L=8192 levels of m=128, paired to 4096 levels of 256
     "penta_L8192_m128": dict(kind="penta", L=8192, m=128, ratio=0.8, scale2=0.3, seed=2),
     # L=16384, m=256, level-dependent, ratio 0.9 (FP64 blocks ~25.8 GB)

