@@ -199,6 +199,32 @@ int mc_residual(mc_chain* chain, const double* pi, double* resid_l1_host);
  */
 int mc_export(mc_chain* chain, int32_t plane, int64_t level0, int64_t count, double* dst_dev);
 
+/*
+ * Direct residual ||Q^T pi||_1 for callers that cannot allocate device
+ * memory.  The paper has no counterpart: this is a library service.  Code
+ * running inside a CUDA graph capture, a serving loop whose device memory is
+ * owned by another allocator or budget, or a plug-in that only holds device
+ * pointers to someone else's data may be unable to call cudaMalloc or to
+ * provide an mc_create workspace; this entry point needs neither and
+ * allocates nothing.
+ *   dn, loc, up: device generator blocks exactly as for mc_create
+ *     ([L][m][m] doubles, row-major, 8-byte aligned).
+ *   pi: device vector of N = L*m doubles.  resid_dev: device output (1 double).
+ *   L: 2 <= L <= 65536 (larger L is rejected with MC_ERR_ARG: the library's
+ *     scratch holds one partial sum per level).  m: 1 <= m <= 256.
+ *   cuda_stream: stream for the work (NULL = legacy default stream).
+ * Scratch: one static device array of 65536 doubles plus a counter (about
+ * 512 KB), kept by every GPU that loads the library until the process exits.
+ * All calls share it and a call leaves its contents behind, so calls whose
+ * work overlaps on the GPU (other streams or threads) race: serialise them.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call outside any stream capture.
+ * Async (the result is in resid_dev when the stream reaches it).
+ * Errors: MC_ERR_ARG, MC_ERR_CUDA.
+ */
+int mc_residual_noalloc(const double* dn, const double* loc, const double* up, int64_t L,
+                        int32_t m, const double* pi, double* resid_dev, void* cuda_stream);
+
 /* Wait for the handle's stream and return (and clear) the device status. */
 int mc_sync(mc_chain* chain);
 

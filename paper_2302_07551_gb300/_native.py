@@ -58,6 +58,8 @@ def load():
     lib.mc_residual.restype = ctypes.c_int
     lib.mc_export.argtypes = [vp, i32, i64, i64, vp]
     lib.mc_export.restype = ctypes.c_int
+    lib.mc_residual_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
+    lib.mc_residual_noalloc.restype = ctypes.c_int
     lib.mc_sync.argtypes = [vp]
     lib.mc_sync.restype = ctypes.c_int
     lib.mc_destroy.argtypes = [vp]
