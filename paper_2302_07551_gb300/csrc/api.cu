@@ -95,6 +95,9 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.wpart = c->wpart;
   a.parity = p1;
   a.P = (L - p1 + 1) / 2;
+  a.hdr = c->hdr;
+  a.reduce_s = 0;
+  a.n_wpart = 2 * c->nw;
   if (ev) CK(cudaEventRecord(ev[0], s));
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[1], s));
@@ -103,18 +106,18 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.wpart = c->wpart + c->nw;
   a.parity = p2;
   a.P = (L - p2 + 1) / 2;
+  a.reduce_s = 1;   // its last block sums the partials of both half-sweeps
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[2], s));
   NormArgs n{};
   n.z = c->z;
   n.x_old = src;
   n.x_new = dst;
-  n.wpart = c->wpart;
+  n.s = &c->hdr->stats[0];
   n.dpart = c->dpart;
   n.hdr = c->hdr;
   n.stats_out = stats_out;
   n.N = c->lay.N;
-  n.n_wpart = 2 * c->nw;
   CK(launch_normalise(n, c->nb_norm, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
   return MC_OK;
@@ -183,19 +186,21 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   c->wpart = (double*)(c->ws + lay.off_wpart);
   c->dpart = (double*)(c->ws + lay.off_dpart);
   c->rpart = (double*)(c->ws + lay.off_rpart);
-  // persistent grids: up to 16 warps per SM, never more warps than levels
+  // persistent grids: as many resident warps as the kernel's occupancy gives,
+  // never more warps than levels
   const int64_t pmax = (lay.L + 1) / 2;
-  int64_t w = 16LL * sms;
+  const int64_t wps = (int64_t)kWarpsPerBlock * phase_blocks_per_sm(lay.m);
+  int64_t w = wps * sms;
   if (w > pmax) w = pmax;
   if (w > kMaxWarps) w = kMaxWarps;
   c->nb_phase = (int)((w + kWarpsPerBlock - 1) / kWarpsPerBlock);
   c->nw = c->nb_phase * kWarpsPerBlock;
-  int64_t wr = 16LL * sms;
+  int64_t wr = wps * sms;
   if (wr > lay.L) wr = lay.L;
   if (wr > kMaxWarps) wr = kMaxWarps;
   c->nb_resid = (int)((wr + kWarpsPerBlock - 1) / kWarpsPerBlock);
   int64_t nbn = (lay.N + 4 * kNormThreads - 1) / (4 * kNormThreads);
-  if (nbn > 2 * sms) nbn = 2 * sms;
+  if (nbn > 8 * sms) nbn = 8 * sms;
   if (nbn > kMaxNormBlocks) nbn = kMaxNormBlocks;
   c->nb_norm = (int)(nbn < 1 ? 1 : nbn);
   if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) {

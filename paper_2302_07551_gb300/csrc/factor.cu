@@ -36,8 +36,8 @@ __global__ void k_layout(const double* __restrict__ dn, const double* __restrict
 
 // LU without pivoting of T_dd (column-major, in A), then X = T_dd^{-1} by
 // forward and backward substitution on the identity, stored as -X = (-T_dd)^{-1}.
-// One CTA per level; A and X live in shared memory (SMEM) or in the LU / NINV
-// planes (large m).  Every step ends with a CTA barrier; all loops are bounded.
+// One CTA per level; A and X live in shared memory (m <= 112).  Every step
+// ends with a CTA barrier; all loops are bounded.
 template <bool SMEM>
 __global__ void __launch_bounds__(256) k_lu_inv(const double* tdd, double* lu,
                                                 double* ninv, int64_t L, int m, int ms,
@@ -102,6 +102,154 @@ __global__ void __launch_bounds__(256) k_lu_inv(const double* tdd, double* lu,
   }
 }
 
+// Blocked LU and inverse for blocks too large for shared memory (m > 112):
+// one 512-thread CTA per level, column panels of kB = 32.
+//   LU (right-looking): factor the panel (rows p0..m-1) in shared memory,
+//   solve U12 = L11^{-1} A12 in shared memory, update the trailing block
+//   A22 -= L21 U12 in place.
+//   Inverse: X = U^{-1} L^{-1} one identity column panel at a time, kept in
+//   shared memory: forward substitution by row panels (triangle by a warp per
+//   right-hand side, rows below by a panel product), then backward
+//   substitution the same way; the panel is stored as -X = (-T_dd)^{-1}.
+constexpr int kB = 32, kLd = 256, kLdU = kB + 1, kBigThreads = 512;
+
+__global__ void __launch_bounds__(kBigThreads, 1) k_factor_big(const double* __restrict__ tdd,
+                                                               double* lu, double* ninv,
+                                                               int64_t L, int m, int ms,
+                                                               Header* hdr) {
+  extern __shared__ double sm[];
+  double* Pan = sm;                  // panel / right-hand sides: [kB][kLd]
+  double* U12 = sm + kB * kLd;       // U12 block: [column][kLdU]
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, wid = tid >> 5;
+  const int nwarp = nt >> 5;
+  const int np = (m + kB - 1) / kB;
+  for (int64_t l = blockIdx.x; l < L; l += gridDim.x) {
+    double* A = lu + (size_t)l * ms;
+    double* X = ninv + (size_t)l * ms;
+    const double* T = tdd + (size_t)l * ms;
+    for (int e = tid; e < m * m; e += nt) A[e] = T[e];
+    __syncthreads();
+    bool ok = true;
+    for (int p = 0; p < np && ok; ++p) {
+      const int p0 = p * kB, w = min(kB, m - p0), nr = m - p0;
+      for (int e = tid; e < w * nr; e += nt) {
+        const int k = e / nr, i = e % nr;
+        Pan[k * kLd + i] = A[(size_t)(p0 + k) * m + p0 + i];
+      }
+      __syncthreads();
+      for (int k = 0; k < w; ++k) {
+        const double piv = Pan[k * kLd + k];
+        if (!(piv != 0.0) || !isfinite(piv)) { ok = false; break; }
+        for (int i = k + 1 + tid; i < nr; i += nt) Pan[k * kLd + i] = Pan[k * kLd + i] / piv;
+        __syncthreads();
+        const int nc = w - k - 1, nrr = nr - k - 1;
+        for (int e = tid; e < nc * nrr; e += nt) {
+          const int j = k + 1 + e / nrr, i = k + 1 + e % nrr;
+          Pan[j * kLd + i] = fma(-Pan[k * kLd + i], Pan[j * kLd + k], Pan[j * kLd + i]);
+        }
+        __syncthreads();
+      }
+      if (!ok) break;
+      for (int e = tid; e < w * nr; e += nt) {
+        const int k = e / nr, i = e % nr;
+        A[(size_t)(p0 + k) * m + p0 + i] = Pan[k * kLd + i];
+      }
+      const int nc2 = m - p0 - w;
+      if (nc2 > 0) {
+        for (int e = tid; e < w * nc2; e += nt) {
+          const int c = e / w, k = e % w;
+          U12[c * kLdU + k] = A[(size_t)(p0 + w + c) * m + p0 + k];
+        }
+        __syncthreads();
+        for (int c = tid; c < nc2; c += nt) {
+          double* u = U12 + c * kLdU;
+          for (int k = 0; k < w; ++k) {
+            const double uk = u[k];
+            for (int i = k + 1; i < w; ++i) u[i] = fma(-Pan[k * kLd + i], uk, u[i]);
+          }
+        }
+        __syncthreads();
+        for (int e = tid; e < w * nc2; e += nt) {
+          const int c = e / w, k = e % w;
+          A[(size_t)(p0 + w + c) * m + p0 + k] = U12[c * kLdU + k];
+        }
+        for (int e = tid; e < nc2 * nc2; e += nt) {
+          const int i = e % nc2, j = e / nc2;
+          double acc = 0.0;
+          for (int k = 0; k < w; ++k) acc = fma(Pan[k * kLd + w + i], U12[j * kLdU + k], acc);
+          double* a = A + (size_t)(p0 + w + j) * m + p0 + w + i;
+          *a = *a - acc;
+        }
+      }
+      __syncthreads();
+    }
+    if (!ok) {
+      if (tid == 0) latch(hdr, MC_ERR_SINGULAR_BLOCK);
+      __syncthreads();
+      continue;
+    }
+    for (int c = 0; c < np; ++c) {
+      const int c0 = c * kB, wc = min(kB, m - c0);
+      double* Y = Pan;
+      for (int e = tid; e < wc * m; e += nt) {
+        const int j = e / m, i = e % m;
+        Y[j * kLd + i] = (i == c0 + j) ? 1.0 : 0.0;
+      }
+      __syncthreads();
+      // forward: L Y = E (rows above c0 stay zero)
+      for (int p = c; p < np; ++p) {
+        const int p0 = p * kB, w = min(kB, m - p0);
+        for (int j = wid; j < wc; j += nwarp) {
+          double y = lane < w ? Y[j * kLd + p0 + lane] : 0.0;
+          for (int k = 0; k < w; ++k) {
+            const double yk = __shfl_sync(0xffffffffu, y, k);
+            if (lane > k && lane < w) y = fma(-A[(size_t)(p0 + k) * m + p0 + lane], yk, y);
+          }
+          if (lane < w) Y[j * kLd + p0 + lane] = y;
+        }
+        __syncthreads();
+        const int nb2 = m - p0 - w;
+        for (int e = tid; e < nb2 * wc; e += nt) {
+          const int i = e % nb2, j = e / nb2;
+          double acc = 0.0;
+          for (int k = 0; k < w; ++k)
+            acc = fma(A[(size_t)(p0 + k) * m + p0 + w + i], Y[j * kLd + p0 + k], acc);
+          Y[j * kLd + p0 + w + i] -= acc;
+        }
+        __syncthreads();
+      }
+      // backward: U X = Y
+      for (int p = np - 1; p >= 0; --p) {
+        const int p0 = p * kB, w = min(kB, m - p0);
+        for (int j = wid; j < wc; j += nwarp) {
+          double y = lane < w ? Y[j * kLd + p0 + lane] : 0.0;
+          for (int k = w - 1; k >= 0; --k) {
+            double xk = 0.0;
+            if (lane == k) xk = y / A[(size_t)(p0 + k) * m + p0 + k];
+            xk = __shfl_sync(0xffffffffu, xk, k);
+            if (lane == k) y = xk;
+            if (lane < k) y = fma(-A[(size_t)(p0 + k) * m + p0 + lane], xk, y);
+          }
+          if (lane < w) Y[j * kLd + p0 + lane] = y;
+        }
+        __syncthreads();
+        for (int e = tid; e < p0 * wc; e += nt) {
+          const int i = e % p0, j = e / p0;
+          double acc = 0.0;
+          for (int k = 0; k < w; ++k) acc = fma(A[(size_t)(p0 + k) * m + i], Y[j * kLd + p0 + k], acc);
+          Y[j * kLd + i] -= acc;
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < wc * m; e += nt) {
+        const int j = e / m, i = e % m;
+        X[(size_t)(c0 + j) * m + i] = -Y[j * kLd + i];
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // W = NINV * T for T in {TLO, TUP} (column-major, per level).
 __global__ void __launch_bounds__(256) k_coupled(const double* __restrict__ ninv,
                                                  const double* __restrict__ tlo,
@@ -151,12 +299,14 @@ cudaError_t launch_factor(double* planes, const Layout& lay, Header* hdr, int co
     k_lu_inv<true><<<nb, 256, smem, s>>>(planes + kPlaneTDD * pe, planes + kPlaneLU * pe,
                                          planes + kPlaneNINV * pe, lay.L, m, lay.ms, hdr);
   } else {
-    // copy TDD into the LU plane, factor in place in global memory
-    cudaError_t e = cudaMemcpyAsync(planes + kPlaneLU * pe, planes + kPlaneTDD * pe,
-                                    lay.plane_bytes, cudaMemcpyDeviceToDevice, s);
+    const size_t bsm = sizeof(double) * (size_t)(kB * kLd + kLd * kLdU);
+    cudaError_t e = cudaFuncSetAttribute(k_factor_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)bsm);
     if (e != cudaSuccess) return e;
-    k_lu_inv<false><<<nb, 256, 0, s>>>(planes + kPlaneLU * pe, planes + kPlaneLU * pe,
-                                       planes + kPlaneNINV * pe, lay.L, m, lay.ms, hdr);
+    int nbb = num_sms;
+    if (nbb > lay.L) nbb = (int)lay.L;
+    k_factor_big<<<nbb, kBigThreads, bsm, s>>>(planes + kPlaneTDD * pe, planes + kPlaneLU * pe,
+                                               planes + kPlaneNINV * pe, lay.L, m, lay.ms, hdr);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess || !coupled) return e;

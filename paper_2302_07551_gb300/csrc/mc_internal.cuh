@@ -53,21 +53,23 @@ struct PhaseArgs {
   const double* src;     // vector read at neighbour levels l-1, l+1
   double* dst;           // z, written at this half-sweep's levels
   double* wpart;         // one level-sum partial per warp
+  Header* hdr;
   int64_t L, P;          // levels, levels in this half-sweep
   int m, ms;
   int parity;            // level of unit u is 2u + parity
+  int reduce_s;          // last block sums the n_wpart partials into hdr->stats[0]
+  int n_wpart;           // partials of both half-sweeps (reduce_s only)
 };
 
 struct NormArgs {
   const double* z;
   const double* x_old;
   double* x_new;
-  const double* wpart;   // 2 * n_warps partials of e^T z
+  const double* s;       // e^T z (hdr->stats[0], written by half-sweep 2)
   double* dpart;         // one per block
   Header* hdr;
   double* stats_out;     // optional extra copy of [s, step, NaN]
   int64_t N;
-  int n_wpart;
 };
 
 struct ResidArgs {
@@ -88,6 +90,7 @@ cudaError_t launch_layout(const double* dn, const double* loc, const double* up,
 cudaError_t launch_factor(double* planes, const Layout& lay, Header* hdr, int coupled,
                           int num_sms, cudaStream_t s);
 cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s);
+int phase_blocks_per_sm(int m);   // resident 256-thread blocks of k_phase per SM
 cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);

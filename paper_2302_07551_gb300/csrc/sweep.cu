@@ -5,20 +5,24 @@
 //                 z_l = (-Q_ll)^{-1} (Q_{l,l-1} x_{l-1} + Q_{l,l+1} x_{l+1})
 //                 (steps 1 and 2 of Algorithm 2);
 //   half-sweep 2: coupled rows, same formula with z in place of x (step 3);
+//                 its last block also reduces e^T z;
 //   normalise:    x_new = z / e^T z,  step = ||x_new - x_old||_1.
 // All Q blocks here are blocks of Q^T, stored column-major (see
 // mc_internal.cuh).
 //
 // Mapping (FP64 pipe bound on GB300: one DFMA per 8 streamed bytes and only
-// ~2 DFMA/clk/SM): one WARP owns one level.  Lane k owns rows k, k+32, ...
+// 2 DFMA/clk/SM): one WARP owns one level.  Lane k owns rows k, k+32, ...
 // (R = ceil(m/32) rows), so every block column j is one coalesced 256-byte
 // load per 32 rows and every multiply-add lands in the lane's own
-// accumulator: no cross-lane reductions, no idle FP64 slots for m % 32 == 0.
-// The vector entry v_j is broadcast with a shuffle from the lane that owns
-// it; the intermediate g = Q_{l,l-1} v + Q_{l,l+1} v of the inverse mode has
-// exactly the same ownership, so the second product needs no shared memory
-// and no barrier.  Warps stream levels with a static stride, and each warp
-// writes one partial of e^T z (fixed order -> bitwise deterministic sums).
+// accumulators: no cross-lane reductions and no idle FP64 slots when
+// m % 32 == 0.  The level's input vectors sit in a per-warp slice of shared
+// memory and v_j, v_{j+1} reach all lanes with one broadcast 16-byte load;
+// the intermediate g of the inverse mode goes through the same slice, so the
+// second product needs no block barrier.  Each row keeps NA independent
+// accumulators (columns interleaved) so that consecutive DFMAs do not wait
+// on each other.  Warps stream levels with a static stride; each warp writes
+// one partial of e^T z and the last block of half-sweep 2 sums them in a
+// fixed order (bitwise deterministic).
 #include <math.h>
 
 #include "mc_internal.cuh"
@@ -37,89 +41,69 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// acc[r] += sum_j M(row_r, j) * v_j  over the m columns of a column-major
-// m x m block M, with v_j held by lane (j % 32) in v[j / 32].
 template <int R>
-__device__ __forceinline__ void gemv_acc(double (&acc)[R], const double* __restrict__ M,
-                                         const double (&v)[R], int m, int lane) {
-  // columns per load batch: a power of two dividing 32, about 16 loads in flight
-  constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;
+struct Tune {
+  static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
+  static constexpr int NA = R <= 2 ? 4 : 2;                            // accumulators per row
+  static constexpr int MINB = R <= 4 ? 3 : 2;                          // blocks per SM
+};
+
+// acc[r][c] += M(row_r, j) * v[j] for the m columns j of a column-major block
+// M; column j feeds accumulator j % NA.  v: per-warp shared slice, zero
+// beyond m (so the pair load at an odd m reads a zero).
+template <int R>
+__device__ __forceinline__ void gemv_acc(double (&acc)[R][Tune<R>::NA],
+                                         const double* __restrict__ M, const double* v, int m,
+                                         int lane) {
+  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
+  for (int j0 = 0; j0 < m; j0 += U) {
+    double t[U][R];
 #pragma unroll
-  for (int kk = 0; kk < R; ++kk) {
-    const int jb = kk * 32;
-    if (jb >= m) break;
-    const int jn = min(32, m - jb);
-    for (int j0 = 0; j0 < jn; j0 += U) {
-      double t[U][R];
+    for (int q = 0; q < U; ++q) {
+      const int j = j0 + q;
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int j = jb + j0 + q;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const int row = lane + 32 * r;
-          t[q][r] = (j0 + q < jn && row < m) ? ld_stream(M + (size_t)j * m + row) : 0.0;
-        }
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        t[q][r] = (j < m && row < m) ? ld_stream(M + (size_t)j * m + row) : 0.0;
       }
+    }
 #pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const double vj = __shfl_sync(kFull, v[kk], (j0 + q) & 31);
+    for (int q = 0; q < U; q += 2) {
+      const double2 vv = *reinterpret_cast<const double2*>(v + j0 + q);
 #pragma unroll
-        for (int r = 0; r < R; ++r) acc[r] = fma(t[q][r], vj, acc[r]);
+      for (int r = 0; r < R; ++r) {
+        acc[r][q % NA] = fma(t[q][r], vv.x, acc[r][q % NA]);
+        acc[r][(q + 1) % NA] = fma(t[q + 1][r], vv.y, acc[r][(q + 1) % NA]);
       }
     }
   }
 }
 
 template <int R>
-__device__ __forceinline__ void load_vec(double (&v)[R], const double* __restrict__ p, int m,
-                                         int lane) {
+__device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
+                                          int lane) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int row = lane + 32 * r;
-    v[r] = row < m ? p[row] : 0.0;
+    v[row] = row < m ? p[row] : 0.0;
   }
 }
 
-template <int R, bool COUPLED>
-__global__ void __launch_bounds__(256) k_phase(PhaseArgs a) {
-  const int lane = threadIdx.x & 31;
-  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int m = a.m;
-  double wsum = 0.0;
-  for (int64_t u = gw; u < a.P; u += nw) {
-    const int64_t l = 2 * u + a.parity;
-    double acc[R];
+template <int R>
+__device__ __forceinline__ void zero_acc(double (&acc)[R][Tune<R>::NA]) {
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0.0;
-    if (l > 0) {
-      double v[R];
-      load_vec<R>(v, a.src + (l - 1) * m, m, lane);
-      gemv_acc<R>(acc, a.A + (size_t)l * a.ms, v, m, lane);
-    }
-    if (l < a.L - 1) {
-      double v[R];
-      load_vec<R>(v, a.src + (l + 1) * m, m, lane);
-      gemv_acc<R>(acc, a.B + (size_t)l * a.ms, v, m, lane);
-    }
-    if (!COUPLED) {
-      double g[R];
+  for (int r = 0; r < R; ++r)
 #pragma unroll
-      for (int r = 0; r < R; ++r) { g[r] = acc[r]; acc[r] = 0.0; }
-      gemv_acc<R>(acc, a.C + (size_t)l * a.ms, g, m, lane);
-    }
-    double ls = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = lane + 32 * r;
-      if (row < m) {
-        a.dst[l * m + row] = acc[r];
-        ls += acc[r];
-      }
-    }
-    wsum += warp_sum(ls);
+    for (int c = 0; c < Tune<R>::NA; ++c) acc[r][c] = 0.0;
+}
+
+template <int R>
+__device__ __forceinline__ double fold(const double (&a)[Tune<R>::NA]) {
+  if constexpr (Tune<R>::NA == 4) {
+    return (a[0] + a[1]) + (a[2] + a[3]);
+  } else {
+    return a[0] + a[1];
   }
-  if (lane == 0) a.wpart[gw] = wsum;
 }
 
 // Deterministic block-wide sum (fixed shuffle tree, fixed warp order).
@@ -134,21 +118,109 @@ __device__ double block_sum(double v, double* sh) {
   return t;
 }
 
+template <int R, bool COUPLED>
+__global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
+  extern __shared__ double vsh[];
+  __shared__ double red[32];
+  __shared__ bool last;
+  constexpr int NA = Tune<R>::NA, W = 32 * R;
+  const int lane = threadIdx.x & 31;
+  double* v_lo = vsh + (threadIdx.x >> 5) * 3 * W;
+  double* v_up = v_lo + W;
+  double* v_g = v_up + W;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int m = a.m;
+  double wsum = 0.0;
+  for (int64_t u = gw; u < a.P; u += nw) {
+    const int64_t l = 2 * u + a.parity;
+    const bool has_lo = l > 0, has_up = l < a.L - 1;
+    if (has_lo) stage_vec<R>(v_lo, a.src + (l - 1) * m, m, lane);
+    if (has_up) stage_vec<R>(v_up, a.src + (l + 1) * m, m, lane);
+    __syncwarp();
+    double acc[R][NA];
+    zero_acc<R>(acc);
+    if (has_lo) gemv_acc<R>(acc, a.A + (size_t)l * a.ms, v_lo, m, lane);
+    if (has_up) gemv_acc<R>(acc, a.B + (size_t)l * a.ms, v_up, m, lane);
+    if (!COUPLED) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
+      __syncwarp();
+      zero_acc<R>(acc);
+      gemv_acc<R>(acc, a.C + (size_t)l * a.ms, v_g, m, lane);
+    }
+    double ls = 0.0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      const double zr = fold<R>(acc[r]);
+      if (row < m) {
+        a.dst[l * m + row] = zr;
+        ls += zr;
+      }
+    }
+    wsum += warp_sum(ls);
+    __syncwarp();   // the slice is rewritten for the next level
+  }
+  if (lane == 0) {
+    a.wpart[gw] = wsum;
+    if (a.reduce_s) __threadfence();
+  }
+  if (!a.reduce_s) return;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned tk = atomicAdd(&a.hdr->ticket[2], 1u);
+    last = (tk == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!last) return;
+  __threadfence();
+  // partials of both half-sweeps, [0, n_wpart) starting at half-sweep 1's
+  const double* parts = a.wpart - (a.n_wpart - nw);
+  double t = 0.0;
+  for (int i = threadIdx.x; i < a.n_wpart; i += blockDim.x) t += __ldcg(parts + i);
+  t = block_sum(t, red);
+  if (threadIdx.x == 0) {
+    a.hdr->stats[0] = t;
+    a.hdr->ticket[2] = 0u;
+  }
+}
+
 __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   __shared__ double sh[32];
   __shared__ bool last;
-  double t = 0.0;
-  for (int i = threadIdx.x; i < a.n_wpart; i += blockDim.x) t += a.wpart[i];
-  const double s = block_sum(t, sh);
+  const double s = *a.s;
   const bool ok = (s > 0.0) && isfinite(s);
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) latch(a.hdr, MC_ERR_BREAKDOWN);
   const double inv = 1.0 / s;
   double d = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
-    const double p = a.z[i] * inv;
-    d += fabs(p - a.x_old[i]);
-    a.x_new[i] = p;
+  const bool vec = ((((uintptr_t)a.x_old) | ((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0;
+  if (vec) {
+    const int64_t n2 = a.N / 2;
+    const double2* z2 = reinterpret_cast<const double2*>(a.z);
+    const double2* x2 = reinterpret_cast<const double2*>(a.x_old);
+    double2* y2 = reinterpret_cast<double2*>(a.x_new);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+      const double2 zz = z2[i], xx = x2[i];
+      double2 p;
+      p.x = zz.x * inv;
+      p.y = zz.y * inv;
+      d += fabs(p.x - xx.x) + fabs(p.y - xx.y);
+      y2[i] = p;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0 && (a.N & 1)) {
+      const int64_t i = a.N - 1;
+      const double p = a.z[i] * inv;
+      d += fabs(p - a.x_old[i]);
+      a.x_new[i] = p;
+    }
+  } else {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
+      const double p = a.z[i] * inv;
+      d += fabs(p - a.x_old[i]);
+      a.x_new[i] = p;
+    }
   }
   d = block_sum(d, sh);
   if (threadIdx.x == 0) {
@@ -164,7 +236,6 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) e += __ldcg(a.dpart + i);
     e = block_sum(e, sh);
     if (threadIdx.x == 0) {
-      a.hdr->stats[0] = s;
       a.hdr->stats[1] = e;
       a.hdr->stats[2] = nan("");
       if (a.stats_out) {
@@ -179,33 +250,34 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
 
 // Direct residual ||Q^T x||_1 from the stored FP64 blocks (Eq. (1)).
 template <int R>
-__global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
+__global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
+  extern __shared__ double vsh[];
   __shared__ double sh[32];
   __shared__ bool last;
+  constexpr int NA = Tune<R>::NA, W = 32 * R;
   const int lane = threadIdx.x & 31;
+  double* v_lo = vsh + (threadIdx.x >> 5) * 3 * W;
+  double* v_dd = v_lo + W;
+  double* v_up = v_dd + W;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int m = a.m;
   double wsum = 0.0;
   for (int64_t l = gw; l < a.L; l += nw) {
-    double acc[R];
-#pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = 0.0;
-    double v[R];
-    if (l > 0) {
-      load_vec<R>(v, a.x + (l - 1) * m, m, lane);
-      gemv_acc<R>(acc, a.TLO + (size_t)l * a.ms, v, m, lane);
-    }
-    load_vec<R>(v, a.x + l * m, m, lane);
-    gemv_acc<R>(acc, a.TDD + (size_t)l * a.ms, v, m, lane);
-    if (l < a.L - 1) {
-      load_vec<R>(v, a.x + (l + 1) * m, m, lane);
-      gemv_acc<R>(acc, a.TUP + (size_t)l * a.ms, v, m, lane);
-    }
+    if (l > 0) stage_vec<R>(v_lo, a.x + (l - 1) * m, m, lane);
+    stage_vec<R>(v_dd, a.x + l * m, m, lane);
+    if (l < a.L - 1) stage_vec<R>(v_up, a.x + (l + 1) * m, m, lane);
+    __syncwarp();
+    double acc[R][NA];
+    zero_acc<R>(acc);
+    if (l > 0) gemv_acc<R>(acc, a.TLO + (size_t)l * a.ms, v_lo, m, lane);
+    gemv_acc<R>(acc, a.TDD + (size_t)l * a.ms, v_dd, m, lane);
+    if (l < a.L - 1) gemv_acc<R>(acc, a.TUP + (size_t)l * a.ms, v_up, m, lane);
     double ls = 0.0;
 #pragma unroll
-    for (int r = 0; r < R; ++r) ls += fabs(acc[r]);
+    for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));
     wsum += warp_sum(ls);
+    __syncwarp();
   }
   if (lane == 0) {
     a.rpart[gw] = wsum;
@@ -213,7 +285,6 @@ __global__ void __launch_bounds__(256) k_residual(ResidArgs a) {
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    __threadfence();
     const unsigned tk = atomicAdd(&a.hdr->ticket[1], 1u);
     last = (tk == gridDim.x - 1);
   }
@@ -258,24 +329,57 @@ __global__ void __launch_bounds__(1024) k_check_scale(const double* x0, double* 
   for (int64_t i = threadIdx.x; i < n; i += blockDim.x) x[i] = x0[i] / s;
 }
 
+template <int R>
+constexpr size_t vec_smem() {
+  return (size_t)kWarpsPerBlock * 3 * 32 * R * sizeof(double);
+}
+
+// Opt a kernel into more than 48 KB of dynamic shared memory (once).
+template <typename K>
+cudaError_t allow_smem(K kernel, size_t bytes, bool& done) {
+  if (done || bytes <= 40 * 1024) return cudaSuccess;
+  const cudaError_t e =
+      cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) done = true;
+  return e;
+}
+
+template <int R, bool C>
+cudaError_t phase_r(const PhaseArgs& a, int nb, cudaStream_t s) {
+  static bool done = false;
+  const cudaError_t e = allow_smem(k_phase<R, C>, vec_smem<R>(), done);
+  if (e != cudaSuccess) return e;
+  k_phase<R, C><<<nb, 256, vec_smem<R>(), s>>>(a);
+  return cudaGetLastError();
+}
+
 template <bool C>
 cudaError_t phase_dispatch(const PhaseArgs& a, int nb, cudaStream_t s) {
-  const int R = (a.m + 31) / 32;
-  switch (R) {
-    case 1: k_phase<1, C><<<nb, 256, 0, s>>>(a); break;
-    case 2: k_phase<2, C><<<nb, 256, 0, s>>>(a); break;
-    case 3: k_phase<3, C><<<nb, 256, 0, s>>>(a); break;
-    case 4: k_phase<4, C><<<nb, 256, 0, s>>>(a); break;
-    case 5: k_phase<5, C><<<nb, 256, 0, s>>>(a); break;
-    case 6: k_phase<6, C><<<nb, 256, 0, s>>>(a); break;
-    case 7: k_phase<7, C><<<nb, 256, 0, s>>>(a); break;
-    case 8: k_phase<8, C><<<nb, 256, 0, s>>>(a); break;
+  switch ((a.m + 31) / 32) {
+    case 1: return phase_r<1, C>(a, nb, s);
+    case 2: return phase_r<2, C>(a, nb, s);
+    case 3: return phase_r<3, C>(a, nb, s);
+    case 4: return phase_r<4, C>(a, nb, s);
+    case 5: return phase_r<5, C>(a, nb, s);
+    case 6: return phase_r<6, C>(a, nb, s);
+    case 7: return phase_r<7, C>(a, nb, s);
+    case 8: return phase_r<8, C>(a, nb, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int R>
+cudaError_t resid_r(const ResidArgs& a, int nb, cudaStream_t s) {
+  static bool done = false;
+  const cudaError_t e = allow_smem(k_residual<R>, vec_smem<R>(), done);
+  if (e != cudaSuccess) return e;
+  k_residual<R><<<nb, 256, vec_smem<R>(), s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
+
+int phase_blocks_per_sm(int m) { return (m + 31) / 32 <= 4 ? 3 : 2; }
 
 cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s) {
   return coupled ? phase_dispatch<true>(a, n_blocks, s) : phase_dispatch<false>(a, n_blocks, s);
@@ -287,19 +391,17 @@ cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s) {
 }
 
 cudaError_t launch_residual(const ResidArgs& a, int nb, cudaStream_t s) {
-  const int R = (a.m + 31) / 32;
-  switch (R) {
-    case 1: k_residual<1><<<nb, 256, 0, s>>>(a); break;
-    case 2: k_residual<2><<<nb, 256, 0, s>>>(a); break;
-    case 3: k_residual<3><<<nb, 256, 0, s>>>(a); break;
-    case 4: k_residual<4><<<nb, 256, 0, s>>>(a); break;
-    case 5: k_residual<5><<<nb, 256, 0, s>>>(a); break;
-    case 6: k_residual<6><<<nb, 256, 0, s>>>(a); break;
-    case 7: k_residual<7><<<nb, 256, 0, s>>>(a); break;
-    case 8: k_residual<8><<<nb, 256, 0, s>>>(a); break;
+  switch ((a.m + 31) / 32) {
+    case 1: return resid_r<1>(a, nb, s);
+    case 2: return resid_r<2>(a, nb, s);
+    case 3: return resid_r<3>(a, nb, s);
+    case 4: return resid_r<4>(a, nb, s);
+    case 5: return resid_r<5>(a, nb, s);
+    case 6: return resid_r<6>(a, nb, s);
+    case 7: return resid_r<7>(a, nb, s);
+    case 8: return resid_r<8>(a, nb, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s) {

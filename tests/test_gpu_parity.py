@@ -35,7 +35,7 @@ def make(L, m, seed=7, dep=True, ratio=0.8):
 
 
 SHAPES = [(64, 8), (37, 5), (2, 1), (3, 33), (130, 64), (21, 100), (9, 256), (64, 1), (16, 32),
-          (11, 160)]
+          (11, 160), (5, 113), (6, 130), (4, 200)]
 
 
 @pytest.mark.parametrize("L,m", SHAPES)
