@@ -66,6 +66,10 @@ def _load():
     lib.or_residual.restype = dbl
     lib.or_solve.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp, dbl, dbl, i64, i64, vp, vp]
     lib.or_solve.restype = i64
+    lib.or_sweep_rhs.argtypes = [i64, i32, i32, vp, vp, vp, vp, vp, vp, vp]
+    lib.or_sweep_rhs.restype = i32
+    lib.or_residual_vec.argtypes = [i64, i32, vp, vp, vp, vp, vp]
+    lib.or_residual_vec.restype = None
     lib.or_threads.argtypes = [i32]
     lib.or_threads.restype = i32
     _lib = lib
@@ -116,6 +120,25 @@ class Chain:
         if rc != 0:
             raise ValueError("bad method")
         return z
+
+    def sweep_rhs(self, x, b, method=STAIR1):
+        """z = M^{-1} (N x + b): the correction step of iterative refinement."""
+        x = _c64(x).reshape(-1)
+        b = _c64(b).reshape(-1)
+        z = np.empty(self.N)
+        rc = _load().or_sweep_rhs(self.L, self.m, int(method), _p(self.Tlo), _p(self.Tup),
+                                  _p(self.LU), _p(self.piv), _p(x), _p(b), _p(z))
+        if rc != 0:
+            raise ValueError("bad method")
+        return z
+
+    def residual_vec(self, x):
+        """r = Q^T x (the vector)."""
+        x = _c64(x).reshape(-1)
+        r = np.empty(self.N)
+        _load().or_residual_vec(self.L, self.m, _p(self.Tlo), _p(self.Tdd), _p(self.Tup), _p(x),
+                                _p(r))
+        return r
 
     def normalised_sweep(self, x, method=STAIR1):
         """One step of Eq. (2): returns (z / e^T z, e^T z, ||z/e^T z - x||_1)."""

@@ -201,6 +201,67 @@ int or_sweep(int64_t L, int m, int method, const double* Tlo, const double* Tup,
   return -1;
 }
 
+/*
+ * One step of the same splitting with a right-hand side:  z = M^{-1} (N x + b).
+ * This is the correction equation of iterative refinement: with r = T pi and
+ * b = -r, the fixed point d of z = M^{-1}(N d - r) solves T d = -r (Eq. (2)
+ * applied to T d = -r instead of T pi = 0).  Stair types follow the steps of
+ * Algorithm 2 with b added to step 1; BGS and BJ as in or_sweep.  b = 0 gives
+ * or_sweep.  Returns 0, or -1 on an unknown method.
+ */
+int or_sweep_rhs(int64_t L, int m, int method, const double* Tlo, const double* Tup,
+                 const double* LU, const int* piv, const double* x, const double* b, double* z) {
+  if (or_sweep(L, m, method, Tlo, Tup, LU, piv, x, z) != 0) return -1;
+  /* z currently holds M^{-1} N x; add M^{-1} b by solving M w = b the same way */
+  const size_t N = (size_t)L * m;
+  double* w = (double*)malloc(sizeof(double) * N);
+  if (method == OR_STAIR1 || method == OR_STAIR2) {
+    const int type = method == OR_STAIR1 ? 1 : 2;
+    for (int64_t l = 0; l < L; ++l)          /* diagonal-only rows: w_l = Q_ll^{-1} b_l */
+      if (stair_diag_only(type, l)) {
+        memcpy(w + (size_t)l * m, b + (size_t)l * m, sizeof(double) * (size_t)m);
+        or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, w + (size_t)l * m);
+      }
+    for (int64_t l = 0; l < L; ++l)          /* coupled rows: w_l = Q_ll^{-1}(b_l - Q_{l,l-1} w_{l-1} - Q_{l,l+1} w_{l+1}) */
+      if (!stair_diag_only(type, l)) {
+        double* acc = (double*)calloc((size_t)m, sizeof(double));
+        if (l > 0) gemv_acc(m, BLK(Tlo, l, m), w + (size_t)(l - 1) * m, acc);
+        if (l < L - 1) gemv_acc(m, BLK(Tup, l, m), w + (size_t)(l + 1) * m, acc);
+        for (int i = 0; i < m; ++i) w[(size_t)l * m + i] = b[(size_t)l * m + i] - acc[i];
+        free(acc);
+        or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, w + (size_t)l * m);
+      }
+  } else if (method == OR_BGS) {
+    for (int64_t l = 0; l < L; ++l) {
+      double* acc = (double*)calloc((size_t)m, sizeof(double));
+      if (l > 0) gemv_acc(m, BLK(Tlo, l, m), w + (size_t)(l - 1) * m, acc);
+      for (int i = 0; i < m; ++i) w[(size_t)l * m + i] = b[(size_t)l * m + i] - acc[i];
+      free(acc);
+      or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, w + (size_t)l * m);
+    }
+  } else {
+    for (int64_t l = 0; l < L; ++l) {
+      memcpy(w + (size_t)l * m, b + (size_t)l * m, sizeof(double) * (size_t)m);
+      or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, w + (size_t)l * m);
+    }
+  }
+  for (size_t i = 0; i < N; ++i) z[i] += w[i];
+  free(w);
+  return 0;
+}
+
+/* The residual vector r = T x (Eq. (1)), from the blocks of T = Q^T. */
+void or_residual_vec(int64_t L, int m, const double* Tlo, const double* Tdd, const double* Tup,
+                     const double* x, double* r) {
+  for (int64_t l = 0; l < L; ++l) {
+    double* acc = r + (size_t)l * m;
+    for (int i = 0; i < m; ++i) acc[i] = 0.0;
+    if (l > 0) gemv_acc(m, BLK(Tlo, l, m), x + (size_t)(l - 1) * m, acc);
+    gemv_acc(m, BLK(Tdd, l, m), x + (size_t)l * m, acc);
+    if (l < L - 1) gemv_acc(m, BLK(Tup, l, m), x + (size_t)(l + 1) * m, acc);
+  }
+}
+
 /* ||T x||_1 computed directly from the blocks of T = Q^T. */
 double or_residual(int64_t L, int m, const double* Tlo, const double* Tdd, const double* Tup,
                    const double* x) {

@@ -145,6 +145,41 @@ def test_sweeps_equal_dense_splittings(L, m):
         assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), meth
 
 
+@pytest.mark.parametrize("L,m", [(7, 3), (8, 4), (5, 1)])
+def test_sweep_with_rhs_equals_dense(L, m):
+    """The refinement step z = M^{-1}(N x + b), against dense M and N."""
+    dn, loc, up = synth.qbd(L, m, 0.8, seed=40 + L, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    T = dense_QT(dn, loc, up)
+    rng = np.random.default_rng(L)
+    x = rng.random(L * m)
+    b = rng.standard_normal(L * m)
+    for meth, M in [(oracle.STAIR1, stair_M(T, L, m, 1)), (oracle.STAIR2, stair_M(T, L, m, 2)),
+                    (oracle.BGS, bgs_M(T, L, m)), (oracle.BJ, bj_M(T, L, m))]:
+        ref = np.linalg.solve(M, (M - T) @ x + b)
+        z = ch.sweep_rhs(x, b, meth)
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), meth
+        assert np.array_equal(ch.sweep_rhs(x, np.zeros_like(b), meth), ch.sweep(x, meth))
+    assert np.allclose(ch.residual_vec(x), T @ x, rtol=1e-14, atol=1e-15)
+
+
+def test_refinement_fixed_point_solves_correction_equation():
+    """Iterating z = M^{-1}(N d - r) drives T d + r to zero (e^T r = 0)."""
+    dn, loc, up = synth.qbd(10, 3, 0.8, seed=2, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    pi = np.full(30, 1 / 30)
+    r = ch.residual_vec(pi)
+    assert abs(r.sum()) < 1e-15
+    d = np.zeros(30)
+    for _ in range(3000):
+        d = ch.sweep_rhs(d, -r)
+    T = dense_QT(dn, loc, up)
+    assert np.abs(T @ d + r).sum() <= 1e-12
+    x = (pi + d) / (pi + d).sum()
+    ref = direct_pi(dn, loc, up)
+    assert np.abs(x - ref).sum() <= 1e-11
+
+
 def test_residual_against_dense():
     dn, loc, up = synth.qbd(9, 4, 0.8, seed=4, level_dependent=True)
     ch = oracle.Chain(dn, loc, up)
