@@ -161,7 +161,8 @@ def run_reference(args):
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps / (Ls / L), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.dtype == "f64" else f"{args.dtype} blocks, f32 sweeps, f64 refinement", "data": "synthetic",
            "config": {"workload": name, "L": L, "m": m, "sample_levels": Ls},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},
@@ -197,7 +198,7 @@ def run_mine(args):
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)
     with torch.cuda.stream(stream):
-        ch = mcl.Chain(*d, apply=args.apply, stream=stream)
+        ch = mcl.Chain(*d, apply=args.apply, stream=stream, dtype=args.dtype)
     del d
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -219,11 +220,24 @@ def run_mine(args):
     # kernel launch (mc_profile) and around the whole region
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    _, prof = ch.profile(x, y, args.steps)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1)
+    if args.dtype == "f64":
+        e0.record(stream)
+        _, prof = ch.profile(x, y, args.steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+    else:
+        # a step = one correction sweep of mixed-precision refinement, with the
+        # FP64 outer step (residual, q, update, renormalisation) every
+        # --refine-every sweeps inside the timed region
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            ch.solve(x0=x, tol=0.0, eps=0.0, maxit=args.steps, check_every=args.refine_every, pi=y)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        _, prof = ch.profile(x, y, min(args.steps, 200))
+        prof_steps = min(args.steps, 200)
     if ws > 1:
         t = torch.tensor([ms], device=dev)
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
@@ -254,10 +268,18 @@ def run_mine(args):
     # vector read once and z written once (16 m bytes); per sweep add reading
     # x and writing pi (16 N bytes) as counted for the whole step.
     nmat = 3 if args.apply == "inverse" else 2
-    bytes_level = 8 * nmat * m * m + 16 * m
+    if args.dtype == "f64":
+        bytes_level = 8 * nmat * m * m + 16 * m
+        sweep_bytes = L * 8 * nmat * m * m + 16 * N
+        prof_steps = args.steps
+    else:
+        # FP32 vectors: neighbour d read, q read, d written (16 m bytes / level)
+        es = 4 if args.dtype == "f32" else 2
+        mat = 2 * es * m * m + (4 * m * m if args.apply == "inverse" else 0)
+        bytes_level = mat + 16 * m
+        sweep_bytes = L * bytes_level
     flops_level = 2 * nmat * m * m
-    sweep_bytes = L * 8 * nmat * m * m + 16 * N
-    half_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * args.steps)
+    half_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * prof_steps)
     half_bytes = bytes_level * L / 2
     half_flops = flops_level * L / 2
     hbm_peak, hbm_src = peaks()
@@ -284,25 +306,33 @@ def run_mine(args):
         # counters taken on an older kernel source do not describe this one
         if key in tj and tj.get("sweep_cu_sha256") == sha:
             traffic = tj[key]["bytes_per_launch"]
+    if args.dtype == "f64":
+        roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
+                "traffic": traffic, "kernel": "k_phase (one half-sweep)",
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (rate measured, profiles/fp64_peak.md)",
+                "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
+    else:
+        roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved_gbs / hbm_peak, "traffic": None,
+                "kernel": "k_phase_lp (one correction half-sweep)", "peak_source": hbm_src}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if args.dtype == "f64" else f"{args.dtype} blocks, f32 sweeps, f64 refinement",
         "data": "synthetic (seeded QBD generator, level-dependent blocks)",
         "config": {"workload": name, "L": L, "m": m, "N": N, "apply": args.apply, "stair": 1,
-                   "block_bytes": L * 8 * nmat * m * m,
+                   "block_bytes": sweep_bytes - 16 * N,
+                   "refine_every": args.refine_every if args.dtype != "f64" else None,
                    "l2": "no flush: the streamed blocks exceed L2 (129 MB) every step",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "gbs_per_sweep": sweep_bytes / (ms / args.steps * 1e-3) / 1e9,
-        "roofline": {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                     "traffic": traffic, "kernel": "k_phase (one half-sweep)",
-                     "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (rate measured, profiles/fp64_peak.md)",
-                     "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                             "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}},
-        "kernel_ms_per_sweep": {"half1": prof["half1_ms"] / args.steps,
-                                "half2": prof["half2_ms"] / args.steps,
-                                "normalise": prof["norm_ms"] / args.steps},
+        "roofline": roof,
+        "kernel_ms_per_sweep": {"half1": prof["half1_ms"] / prof_steps,
+                                "half2": prof["half2_ms"] / prof_steps,
+                                "normalise": prof["norm_ms"] / prof_steps},
         "e2e": {"value": ws * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N + 8 * 3},
         "gpu_launches": prof["launches"],
@@ -314,6 +344,46 @@ def run_mine(args):
     ch.close()
     if ws > 1:
         torch.distributed.destroy_process_group()
+
+
+def run_solve(args):
+    """Time to solution: one full solve of the workload to ||Q^T pi||_1 <= tol
+    for FP64 and the mixed-precision forms, with the result's distance to the
+    FP64 solution (the FP64 GPU path itself matches the CPU oracle to 1e-10 on
+    every oracle-sized case of the test suite)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2302_07551_gb300 as mcl
+
+    torch.cuda.set_device(0)
+    name = args.workload
+    L, m = synth.workload_shape(name)
+    blocks = synth.workload(name)
+    d = [torch.from_numpy(b).cuda() for b in blocks]
+    del blocks
+    torch.cuda.synchronize()
+    rows = []
+    ref = None
+    for dtype in ("f64", "f32", "bf16"):
+        ch = mcl.Chain(*d, apply=args.apply, dtype=dtype)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pi, res = ch.solve(tol=args.tol, maxit=10_000_000, check_every=args.refine_every)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        p = pi.cpu().numpy()
+        if ref is None:
+            ref = p
+        rows.append({"dtype": dtype, "seconds": t, "sweeps": res["sweeps"],
+                     "residual": res["residual"], "converged": res["converged"],
+                     "rel_l1_vs_f64": float(np.abs(p - ref).sum() / np.abs(ref).sum()),
+                     "ms_per_sweep": 1e3 * t / max(res["sweeps"], 1)})
+        ch.close()
+    print(json.dumps({"mode": "time_to_solution", "workload": name, "L": L, "m": m,
+                      "apply": args.apply, "tol": args.tol, "refine_every": args.refine_every,
+                      "results": rows}), flush=True)
 
 
 def measure_fp64_peak():
@@ -349,6 +419,11 @@ def main():
     ap.add_argument("--impl", default="mine", choices=["mine", "reference"])
     ap.add_argument("--workload", default="qbd_L32768_m64")
     ap.add_argument("--apply", default="inverse", choices=["inverse", "coupled"])
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--refine-every", type=int, default=64)
+    ap.add_argument("--solve", action="store_true",
+                    help="time one full solve to --tol per dtype instead of sweeps")
+    ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--measure-fp64-peak", action="store_true")
@@ -360,6 +435,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.solve:
+        run_solve(args)
     else:
         run_mine(args)
 

@@ -51,8 +51,19 @@ typedef enum {
   MC_ERR_TIMEOUT = 8          /* a bounded device-side wait gave up            */
 } mc_status;
 
-/* Storage type of the blocks streamed by the sweep.  This version: MC_F64. */
-typedef enum { MC_F64 = 0 } mc_dtype;
+/*
+ * Storage type of the blocks streamed by mc_solve's sweeps.
+ *   MC_F64: plain FP64 staircase iteration of Eq. (2) (Algorithm 2).
+ *   MC_F32, MC_BF16: mixed-precision iterative refinement (a library design,
+ *     not in the paper): each outer step forms r = Q^T pi and
+ *     q = (-T_dd)^{-1} r in FP64, runs check_every staircase sweeps of the
+ *     correction equation Q^T d = -r (d <- M^{-1}(N d - r), Eq. (2) with a
+ *     right-hand side) in FP32 arithmetic on blocks stored in FP32, or in BF16
+ *     with one power-of-two scale per block, then updates
+ *     pi <- (pi + d) / e^T(pi + d) in FP64.  (-T_dd)^{-1} is stored in FP32.
+ *     Requires m % 4 == 0.  The FP64 blocks stay resident for the residual.
+ */
+typedef enum { MC_F64 = 0, MC_F32 = 1, MC_BF16 = 2 } mc_dtype;
 
 /*
  * How the diagonal-block solves Q_{i,i}^{-1} of Algorithm 2 (steps 2 and 3)
@@ -85,7 +96,7 @@ typedef struct {
   int32_t m;       /* phases per level (block size), 1 <= m <= 256              */
   int32_t stair;   /* 1: stair matrix of type 1 (default), 2: type 2 (Sect. 2)  */
   int32_t apply;   /* mc_apply                                                  */
-  int32_t dtype;   /* mc_dtype; must be MC_F64                                  */
+  int32_t dtype;   /* mc_dtype (MC_F32 / MC_BF16 need m % 4 == 0)               */
 } mc_desc;
 
 typedef struct {

@@ -11,7 +11,8 @@ MC_OK, MC_ERR_ARG, MC_ERR_WORKSPACE, MC_ERR_CUDA = 0, 1, 2, 3
 MC_ERR_SINGULAR_BLOCK, MC_ERR_NOT_FACTORED, MC_ERR_BREAKDOWN = 4, 5, 6
 MC_ERR_NO_CONVERGENCE, MC_ERR_TIMEOUT = 7, 8
 MC_APPLY_INVERSE, MC_APPLY_COUPLED = 0, 1
-MC_F64 = 0
+MC_F64, MC_F32, MC_BF16 = 0, 1, 2
+DTYPES = {"f64": MC_F64, "f32": MC_F32, "bf16": MC_BF16}
 PLANES = {"tlo": 0, "tup": 1, "tdd": 2, "lu": 3, "ninv": 4, "wlo": 5, "wup": 6}
 
 

@@ -23,11 +23,14 @@ class Chain:
     dn, loc, up: float64 CUDA tensors (L, m, m), generator blocks of Q
     (row-major): dn[l] = Q[l, l-1], loc[l] = Q[l, l], up[l] = Q[l, l+1].
     stair: 1 or 2 (stair matrix type).  apply: "inverse" or "coupled".
+    dtype: "f64" (plain FP64 iteration) or "f32" / "bf16" (mixed-precision
+    refinement in solve(); check_every = correction sweeps per outer step).
     The library copies the blocks into its workspace (a torch uint8 tensor
     owned by this object); the inputs may be freed after construction.
     """
 
-    def __init__(self, dn, loc, up, stair=1, apply="inverse", stream=None, factor=True):
+    def __init__(self, dn, loc, up, stair=1, apply="inverse", stream=None, factor=True,
+                 dtype="f64"):
         lib = nat.load()
         for t, n in ((dn, "dn"), (loc, "loc"), (up, "up")):
             _need(t, loc.shape, n)
@@ -36,7 +39,8 @@ class Chain:
         self.device = loc.device
         self.desc = nat.McDesc(self.L, self.m, int(stair),
                                nat.MC_APPLY_COUPLED if apply == "coupled" else nat.MC_APPLY_INVERSE,
-                               nat.MC_F64)
+                               nat.DTYPES[dtype])
+        self.dtype = dtype
         self.apply = apply
         nbytes = lib.mc_workspace_bytes(ctypes.byref(self.desc))
         if nbytes == 0:

@@ -31,7 +31,8 @@ static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 static bool desc_ok(const mc_desc* d) {
   return d && d->L >= 2 && d->L <= (int64_t)1 << 31 && d->m >= 1 && d->m <= kMaxM &&
          (d->stair == 1 || d->stair == 2) &&
-         (d->apply == MC_APPLY_INVERSE || d->apply == MC_APPLY_COUPLED) && d->dtype == MC_F64;
+         (d->apply == MC_APPLY_INVERSE || d->apply == MC_APPLY_COUPLED) &&
+         (d->dtype == MC_F64 || ((d->dtype == MC_F32 || d->dtype == MC_BF16) && d->m % 4 == 0));
 }
 
 Layout make_layout(const mc_desc& d) {
@@ -60,6 +61,27 @@ Layout make_layout(const mc_desc& d) {
   o += round_up(kMaxNormBlocks * sizeof(double), 256);
   y.off_rpart = o;
   o += round_up(kMaxWarps * sizeof(double), 256);
+  y.lp = d.dtype == MC_F32 ? 1 : d.dtype == MC_BF16 ? 2 : 0;
+  if (y.lp) {
+    const size_t es = y.lp == 1 ? 4 : 2;
+    const size_t mm = (size_t)d.m * d.m;
+    y.lp_bs = (int64_t)(round_up(mm * es, 256) / es);
+    y.lp_cbs = (int64_t)(round_up(mm * 4, 256) / 4);
+    y.off_lpA = o;
+    o += round_up((size_t)d.L * y.lp_bs * es, 256);
+    y.off_lpB = o;
+    o += round_up((size_t)d.L * y.lp_bs * es, 256);
+    y.off_lpC = o;
+    if (d.apply == MC_APPLY_INVERSE) o += round_up((size_t)d.L * y.lp_cbs * 4, 256);
+    y.off_sc = o;
+    o += round_up((size_t)d.L * 2 * sizeof(float), 256);
+    y.off_q = o;
+    o += round_up((size_t)y.N * 4, 256);
+    y.off_d = o;
+    o += round_up((size_t)y.N * 4, 256);
+    y.off_bpart = o;
+    o += round_up(kMaxNormBlocks * sizeof(double), 256);
+  }
   y.total = o;
   return y;
 }
@@ -123,12 +145,14 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   return MC_OK;
 }
 
-static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s) {
+static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float* q = nullptr) {
   const size_t pe = c->lay.plane_bytes / sizeof(double);
   ResidArgs r{};
   r.TLO = c->planes + kPlaneTLO * pe;
   r.TDD = c->planes + kPlaneTDD * pe;
   r.TUP = c->planes + kPlaneTUP * pe;
+  r.NINV = c->planes + kPlaneNINV * pe;
+  r.q = q;
   r.x = x;
   r.rpart = c->rpart;
   r.hdr = c->hdr;
@@ -138,6 +162,53 @@ static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s) {
   r.ms = c->lay.ms;
   CK(launch_residual(r, c->nb_resid, s));
   return MC_OK;
+}
+
+// ---- mixed-precision refinement (dtype MC_F32 / MC_BF16) -------------------------
+static const void* lpA(mc_chain* c) { return c->ws + c->lay.off_lpA; }
+static const void* lpB(mc_chain* c) { return c->ws + c->lay.off_lpB; }
+static const float* lpC(mc_chain* c) { return (const float*)(c->ws + c->lay.off_lpC); }
+static float* lpSc(mc_chain* c) { return (float*)(c->ws + c->lay.off_sc); }
+static float* lpQ(mc_chain* c) { return (float*)(c->ws + c->lay.off_q); }
+static float* lpD(mc_chain* c) { return (float*)(c->ws + c->lay.off_d); }
+
+// One correction sweep d <- M^{-1}(N d - r) in low precision (two launches).
+static int enqueue_lp_sweep(mc_chain* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const int p1 = c->d.stair == 1 ? 0 : 1;
+  const int bf16 = c->lay.lp == 2, coupled = c->d.apply == MC_APPLY_COUPLED;
+  if (ev) CK(cudaEventRecord(ev[0], s));
+  CK(launch_phase_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m, p1,
+                     c->lay.lp_bs, c->lay.lp_cbs, bf16, coupled, c->nb_phase, s));
+  if (ev) CK(cudaEventRecord(ev[1], s));
+  CK(launch_phase_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m, 1 - p1,
+                     c->lay.lp_bs, c->lay.lp_cbs, bf16, coupled, c->nb_phase, s));
+  if (ev) CK(cudaEventRecord(ev[2], s));
+  return MC_OK;
+}
+
+// One outer step on the iterate xa: `inner` correction sweeps from d = 0 (q
+// must hold (-T_dd)^{-1} r for the current xa), pi <- (pi + d)/e^T(pi + d)
+// with the step error, then r and q of the new iterate.
+static int enqueue_refine_step(mc_chain* c, int inner, cudaStream_t s) {
+  CK(cudaMemsetAsync(lpD(c), 0, (size_t)c->lay.N * sizeof(float), s));
+  for (int k = 0; k < inner; ++k) {
+    const int rc = enqueue_lp_sweep(c, s);
+    if (rc != MC_OK) return rc;
+  }
+  double* bpart = (double*)(c->ws + c->lay.off_bpart);
+  CK(launch_update(c->xa, lpD(c), c->xb, c->lay.N, bpart, c->nb_norm, c->hdr, &c->hdr->stats[0],
+                   s));
+  NormArgs n{};
+  n.z = c->xb;
+  n.x_old = c->xa;
+  n.x_new = c->xa;
+  n.s = &c->hdr->stats[0];
+  n.dpart = c->dpart;
+  n.hdr = c->hdr;
+  n.stats_out = nullptr;
+  n.N = c->lay.N;
+  CK(launch_normalise(n, c->nb_norm, s));
+  return enqueue_residual(c, c->xa, s, lpQ(c));
 }
 
 // Wait for the stream, fetch the header, clear a latched status.
@@ -230,6 +301,18 @@ int mc_factor(mc_chain* c) {
   c->factored = 0;
   CK(launch_factor(c->planes, c->lay, c->hdr, c->d.apply == MC_APPLY_COUPLED, c->num_sms,
                    c->user));
+  if (c->lay.lp) {
+    const size_t pe = c->lay.plane_bytes / sizeof(double);
+    const int bf16 = c->lay.lp == 2;
+    const bool coupled = c->d.apply == MC_APPLY_COUPLED;
+    CK(launch_lp_convert(c->planes + (coupled ? kPlaneWLO : kPlaneTLO) * pe, c->ws + c->lay.off_lpA,
+                         bf16, lpSc(c), 2, c->lay, c->lay.lp_bs, c->user));
+    CK(launch_lp_convert(c->planes + (coupled ? kPlaneWUP : kPlaneTUP) * pe, c->ws + c->lay.off_lpB,
+                         bf16, lpSc(c) + 1, 2, c->lay, c->lay.lp_bs, c->user));
+    if (!coupled)
+      CK(launch_lp_convert(c->planes + kPlaneNINV * pe, c->ws + c->lay.off_lpC, 0, nullptr, 0,
+                           c->lay, c->lay.lp_cbs, c->user));
+  }
   const int st = sync_header(c);
   if (st != MC_OK) return st;
   c->factored = 1;
@@ -259,8 +342,24 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   size_t made = 0;
   for (; made < ne; ++made)
     if (cudaEventCreate(&ev[made]) != cudaSuccess) { rc = MC_ERR_CUDA; break; }
-  for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
-    rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out, nullptr, c->user, ev + 4 * k);
+  if (c->lay.lp) {
+    // low-precision chains: time the correction sweeps of refinement, with
+    // r and q of x_in (the FP64 x_out is left equal to x_in)
+    if (cudaMemcpyAsync(c->xa, x_in, (size_t)c->lay.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->user) != cudaSuccess ||
+        cudaMemsetAsync(lpD(c), 0, (size_t)c->lay.N * sizeof(float), c->user) != cudaSuccess ||
+        cudaMemcpyAsync(x_out, x_in, (size_t)c->lay.N * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->user) != cudaSuccess)
+      rc = MC_ERR_CUDA;
+    if (rc == MC_OK) rc = enqueue_residual(c, c->xa, c->user, lpQ(c));
+    for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k) {
+      rc = enqueue_lp_sweep(c, c->user, ev + 4 * k);
+      if (rc == MC_OK && cudaEventRecord(ev[4 * k + 3], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+    }
+  } else {
+    for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
+      rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out, nullptr, c->user, ev + 4 * k);
+  }
   double t[3] = {0.0, 0.0, 0.0};
   if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
   for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
@@ -332,6 +431,81 @@ static int capture_chunk(mc_chain* c, int chunk, int with_resid) {
   return MC_OK;
 }
 
+// Mixed-precision solve: outer FP64 refinement steps of check_every
+// low-precision correction sweeps each; the iterate is xa (already set).
+static int solve_refine(mc_chain* c, double* pi, double tol, double eps, int64_t maxit,
+                        int32_t inner, mc_result* res) {
+  const int64_t N = c->lay.N;
+  int rc = enqueue_residual(c, c->xa, c->user, lpQ(c));
+  if (rc != MC_OK) return rc;
+  int st = sync_header(c);
+  if (st != MC_OK) return st;
+  double r = c->hh->stats[2], d = NAN, d_prev = NAN, kappa = NAN;
+  int64_t k = 0;
+  int converged = (tol > 0.0 && r <= tol);
+  while (!converged && k < maxit) {
+    const int64_t chunk = (maxit - k < inner) ? (maxit - k) : inner;
+    if (chunk == inner) {
+      if (!c->gexec || c->g_chunk != inner || c->g_resid != 2) {
+        if (c->gexec) {
+          cudaGraphExecDestroy(c->gexec);
+          c->gexec = nullptr;
+        }
+        CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
+        rc = enqueue_refine_step(c, inner, c->cap);
+        if (rc == MC_OK && cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost,
+                                           c->cap) != cudaSuccess)
+          rc = MC_ERR_CUDA;
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(c->cap, &g);
+        if (rc != MC_OK || e != cudaSuccess) {
+          if (g) cudaGraphDestroy(g);
+          cudaGetLastError();
+          return MC_ERR_CUDA;
+        }
+        const cudaError_t e2 = cudaGraphInstantiate(&c->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) {
+          c->gexec = nullptr;
+          return MC_ERR_CUDA;
+        }
+        c->g_chunk = inner;
+        c->g_resid = 2;
+      }
+      CK(cudaGraphLaunch(c->gexec, c->user));
+      CK(cudaStreamSynchronize(c->user));
+    } else {
+      rc = enqueue_refine_step(c, (int)chunk, c->user);
+      if (rc != MC_OK) return rc;
+      CK(cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->user));
+      CK(cudaStreamSynchronize(c->user));
+    }
+    k += chunk;
+    st = c->hh->status;
+    if (st != 0) {
+      CK(cudaMemsetAsync(&c->hdr->status, 0, sizeof(int32_t), c->user));
+      CK(cudaStreamSynchronize(c->user));
+      return st;
+    }
+    d = c->hh->stats[1];
+    r = c->hh->stats[2];
+    if (d_prev > 0.0 && d > 0.0) kappa = pow(d / d_prev, 1.0 / (double)chunk);
+    d_prev = d;
+    if ((tol > 0.0 && r <= tol) || (eps > 0.0 && d <= eps)) converged = 1;
+  }
+  CK(cudaMemcpyAsync(pi, c->xa, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->user));
+  CK(cudaStreamSynchronize(c->user));
+  if (res) {
+    res->sweeps = k;
+    res->residual_l1 = r;
+    res->step_l1 = d;
+    res->contraction = kappa;
+    res->converged = converged;
+  }
+  if (!converged && (tol > 0.0 || eps > 0.0)) return MC_ERR_NO_CONVERGENCE;
+  return MC_OK;
+}
+
 int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, int64_t maxit,
              int32_t check_every, mc_result* res) {
   if (!c || !pi || maxit < 1 || check_every < 1) return MC_ERR_ARG;
@@ -345,6 +519,7 @@ int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, 
   }
   int st = sync_header(c);
   if (st != MC_OK) return st;
+  if (c->lay.lp) return solve_refine(c, pi, tol, eps, maxit, check_every, res);
   const int with_resid = tol > 0.0;
   int64_t k = 0;
   double d = NAN, d_prev = NAN, r = NAN, kappa = NAN;

@@ -1,0 +1,326 @@
+// Mixed-precision staircase sweeps for iterative refinement.
+//
+// Outer step (FP64): r = Q^T pi (direct, from the FP64 blocks), q = (-T_dd)^{-1} r.
+// Inner sweeps (FP32 arithmetic): the staircase step of Algorithm 2 applied to
+// the correction equation T d = -r, i.e. d <- M^{-1}(N d - r), which on every
+// block row reads
+//     d_l = (-T_dd)^{-1}(T_lo d_{l-1} + T_up d_{l+1}) + q_l
+//  (inverse mode)  or  W_lo d_{l-1} + W_up d_{l+1} + q_l  (coupled mode),
+// half-sweep 1 on the diagonal-only rows, half-sweep 2 on the coupled rows,
+// in place on one FP32 vector d that starts at zero.
+// Update (FP64): pi <- (pi + d) / e^T(pi + d).
+//
+// Storage of the streamed blocks: FP32, or BF16 with one power-of-two scale per
+// block (B = 2^e * B', max |B'| < 1), applied to the input vector in FP32.
+// (-T_dd)^{-1} of the inverse mode is stored in FP32.  Lane loads are 8 bytes:
+// V = 2 FP32 or 4 BF16 consecutive rows per lane, groups of 32 V rows.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+
+namespace {
+
+template <typename T>
+struct Pack;
+template <>
+struct Pack<float> {
+  static constexpr int V = 2;
+  using Raw = float2;
+  __device__ static __forceinline__ Raw load(const float* p) {
+    return __ldcs(reinterpret_cast<const float2*>(p));
+  }
+  __device__ static __forceinline__ Raw zero() { return make_float2(0.0f, 0.0f); }
+  __device__ static __forceinline__ float get(const Raw& r, int e) { return e == 0 ? r.x : r.y; }
+};
+template <>
+struct Pack<__nv_bfloat16> {
+  static constexpr int V = 4;
+  using Raw = uint2;
+  __device__ static __forceinline__ Raw load(const __nv_bfloat16* p) {
+    return __ldcs(reinterpret_cast<const uint2*>(p));
+  }
+  __device__ static __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
+  // bf16 -> fp32 is exact: the 16 bits become the high half of the float
+  __device__ static __forceinline__ float get(const Raw& r, int e) {
+    const unsigned w = (e < 2) ? r.x : r.y;
+    return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+  }
+};
+
+// BF16 read two rows per lane (4-byte loads), for blocks of at most 128 rows
+// where four-row loads would leave lanes idle.
+struct Bf16x2 {
+  unsigned short bits;   // one bf16, addressed in pairs
+};
+template <>
+struct Pack<Bf16x2> {
+  static constexpr int V = 2;
+  using Raw = unsigned int;
+  __device__ static __forceinline__ Raw load(const Bf16x2* p) {
+    return __ldcs(reinterpret_cast<const unsigned int*>(p));
+  }
+  __device__ static __forceinline__ Raw zero() { return 0u; }
+  __device__ static __forceinline__ float get(const Raw& r, int e) {
+    return __uint_as_float(e ? (r & 0xffff0000u) : (r << 16));
+  }
+};
+
+// acc[g][e] += M(row(g,e), j) * v[j], row(g,e) = 32 V g + V lane + e, for the
+// m columns of a column-major block M of element type T.  U columns per
+// batch so that U * G = 32 packed 8-byte loads per lane are in flight.
+template <typename T, int G>
+__device__ __forceinline__ void gemv_lp(float (&acc)[G][Pack<T>::V], const T* __restrict__ M,
+                                        const float* v, int m, int lane) {
+  constexpr int V = Pack<T>::V, U = (32 / G) < 8 ? 8 : (32 / G);
+  using Raw = typename Pack<T>::Raw;
+  for (int j0 = 0; j0 < m; j0 += U) {
+    Raw t[U][G];
+#pragma unroll
+    for (int q = 0; q < U; ++q)
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int row = 32 * V * g + V * lane;
+        t[q][g] = (j0 + q < m && row < m) ? Pack<T>::load(M + (size_t)(j0 + q) * m + row)
+                                          : Pack<T>::zero();
+      }
+#pragma unroll
+    for (int q = 0; q < U; q += 4) {
+      const float4 vv = *reinterpret_cast<const float4*>(v + j0 + q);
+      const float vq[4] = {vv.x, vv.y, vv.z, vv.w};
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+#pragma unroll
+        for (int g = 0; g < G; ++g)
+#pragma unroll
+          for (int e = 0; e < V; ++e)
+            acc[g][e] = fmaf(Pack<T>::get(t[q + h][g], e), vq[h], acc[g][e]);
+    }
+  }
+}
+
+struct LpArgs {
+  const void* A;       // T_lo or W_lo plane (element type T)
+  const void* B;       // T_up or W_up plane
+  const float* C;      // (-T_dd)^{-1} in FP32 (inverse mode)
+  const float* sc;     // per level: scale of A, scale of B
+  float* d;            // iterate, updated in place
+  const float* q;      // (-T_dd)^{-1} r
+  int64_t L, P;
+  int m, parity;
+  int64_t abs_, cbs;   // block strides in elements (A/B planes, C plane)
+};
+
+// One half-sweep of the correction iteration (one warp per level).
+template <typename T, int G, int GF, bool COUPLED>
+__global__ void __launch_bounds__(256) k_phase_lp(LpArgs a) {
+  extern __shared__ float fsh[];
+  constexpr int V = Pack<T>::V, W = 32 * V * G, WF = 64 * GF;
+  constexpr int SL = (W > WF ? W : WF);
+  const int lane = threadIdx.x & 31;
+  float* v_lo = fsh + (threadIdx.x >> 5) * 3 * SL;
+  float* v_up = v_lo + SL;
+  float* v_g = v_up + SL;
+  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int m = a.m;
+  const T* Ap = reinterpret_cast<const T*>(a.A);
+  const T* Bp = reinterpret_cast<const T*>(a.B);
+  for (int64_t u = gw; u < a.P; u += nw) {
+    const int64_t l = 2 * u + a.parity;
+    const bool has_lo = l > 0, has_up = l < a.L - 1;
+    const float s_lo = a.sc[2 * l], s_up = a.sc[2 * l + 1];
+    for (int i = lane; i < SL; i += 32) {
+      v_lo[i] = (has_lo && i < m) ? a.d[(l - 1) * m + i] * s_lo : 0.0f;
+      v_up[i] = (has_up && i < m) ? a.d[(l + 1) * m + i] * s_up : 0.0f;
+    }
+    __syncwarp();
+    float acc[G][V];
+#pragma unroll
+    for (int g = 0; g < G; ++g)
+#pragma unroll
+      for (int e = 0; e < V; ++e) acc[g][e] = 0.0f;
+    if (has_lo) gemv_lp<T, G>(acc, Ap + l * a.abs_, v_lo, m, lane);
+    if (has_up) gemv_lp<T, G>(acc, Bp + l * a.abs_, v_up, m, lane);
+    if (COUPLED) {
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int row = 32 * V * g + V * lane;
+        if (row < m)
+#pragma unroll
+          for (int e = 0; e < V; ++e) a.d[l * m + row + e] = acc[g][e] + a.q[l * m + row + e];
+      }
+    } else {
+      for (int i = lane; i < SL; i += 32) v_g[i] = 0.0f;
+      __syncwarp();
+#pragma unroll
+      for (int g = 0; g < G; ++g) {
+        const int row = 32 * V * g + V * lane;
+        if (row < m)
+#pragma unroll
+          for (int e = 0; e < V; ++e) v_g[row + e] = acc[g][e];
+      }
+      __syncwarp();
+      float acc2[GF][2];
+#pragma unroll
+      for (int g = 0; g < GF; ++g) acc2[g][0] = acc2[g][1] = 0.0f;
+      gemv_lp<float, GF>(acc2, a.C + l * a.cbs, v_g, m, lane);
+#pragma unroll
+      for (int g = 0; g < GF; ++g) {
+        const int row = 64 * g + 2 * lane;
+        if (row < m) {
+          a.d[l * m + row] = acc2[g][0] + a.q[l * m + row];
+          a.d[l * m + row + 1] = acc2[g][1] + a.q[l * m + row + 1];
+        }
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Convert one FP64 block (column-major, stride ms) to FP32 or to BF16 with a
+// power-of-two scale: one CTA per (level, block).
+template <typename T>
+__global__ void __launch_bounds__(256) k_lp_convert(const double* __restrict__ src, T* dst,
+                                                    float* sc, int sc_stride, int64_t L, int m,
+                                                    int ms, int64_t dbs) {
+  __shared__ double red[8];
+  const int64_t l = blockIdx.x;
+  if (l >= L) return;
+  const double* s = src + (size_t)l * ms;
+  const int mm = m * m;
+  double mx = 0.0;
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) mx = fmax(mx, fabs(s[e]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  mx = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmax(mx, red[w]);
+  int ex = 0;
+  if (sizeof(T) == 2 && mx > 0.0) frexp(mx, &ex);   // mx = f 2^ex, f in [0.5, 1)
+  const double inv = ldexp(1.0, -ex);
+  for (int e = threadIdx.x; e < mm; e += blockDim.x) {
+    if constexpr (sizeof(T) == 2) {
+      dst[(size_t)l * dbs + e] = __double2bfloat16(s[e] * inv);
+    } else {
+      dst[(size_t)l * dbs + e] = (T)s[e];
+    }
+  }
+  if (threadIdx.x == 0 && sc) sc[(size_t)l * sc_stride] = (float)ldexp(1.0, ex);
+}
+
+// pi_tmp = pi + d (FP64) with the sum reduced by the last block into s_out.
+__global__ void __launch_bounds__(256) k_update(const double* __restrict__ pi,
+                                                const float* __restrict__ d, double* out,
+                                                int64_t N, double* bpart, Header* hdr,
+                                                double* s_out) {
+  __shared__ double sh[32];
+  __shared__ bool last;
+  double t = 0.0;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = pi[i] + (double)d[i];
+    out[i] = v;
+    t += v;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = t;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double b = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += sh[w];
+    bpart[blockIdx.x] = b;
+    __threadfence();
+    last = (atomicAdd(&hdr->ticket[3], 1u) == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last && threadIdx.x == 0) {
+    __threadfence();
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(bpart + b);
+    *s_out = s;
+    hdr->ticket[3] = 0u;
+  }
+}
+
+template <typename T, int G, int GF, bool C>
+cudaError_t lp_launch(const LpArgs& a, int nb, cudaStream_t s) {
+  constexpr int V = Pack<T>::V, W = 32 * V * G, WF = 64 * GF;
+  constexpr int SL = (W > WF ? W : WF);
+  const size_t smem = (size_t)kWarpsPerBlock * 3 * SL * sizeof(float);
+  static bool done = false;
+  if (!done && smem > 40 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(
+        k_phase_lp<T, G, GF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  k_phase_lp<T, G, GF, C><<<nb, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename T, bool C>
+cudaError_t lp_dispatch(const LpArgs& a, int nb, cudaStream_t s) {
+  constexpr int V = Pack<T>::V;
+  const int G = (a.m + 32 * V - 1) / (32 * V);
+  const int GF = (a.m + 63) / 64;
+  if (GF == 1) return lp_launch<T, 1, 1, C>(a, nb, s);
+  if (GF == 2) return G == 1 ? lp_launch<T, 1, 2, C>(a, nb, s) : lp_launch<T, 2, 2, C>(a, nb, s);
+  if (GF <= 4) {
+    if (G == 1) return lp_launch<T, 1, 4, C>(a, nb, s);
+    if (G == 2) return lp_launch<T, 2, 4, C>(a, nb, s);
+    return lp_launch<T, 4, 4, C>(a, nb, s);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_lp_convert(const double* src, void* dst, int bf16, float* sc, int sc_stride,
+                              const Layout& lay, int64_t dbs, cudaStream_t s) {
+  const int nb = (int)lay.L;
+  if (bf16)
+    k_lp_convert<__nv_bfloat16><<<nb, 256, 0, s>>>(src, (__nv_bfloat16*)dst, sc, sc_stride, lay.L,
+                                                   lay.m, lay.ms, dbs);
+  else
+    k_lp_convert<float><<<nb, 256, 0, s>>>(src, (float*)dst, sc, sc_stride, lay.L, lay.m, lay.ms,
+                                           dbs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_lp(const void* A, const void* B, const float* C, const float* sc,
+                            float* d, const float* q, int64_t L, int m, int parity,
+                            int64_t abs_, int64_t cbs, int bf16, int coupled, int nb,
+                            cudaStream_t s) {
+  LpArgs a{};
+  a.A = A;
+  a.B = B;
+  a.C = C;
+  a.sc = sc;
+  a.d = d;
+  a.q = q;
+  a.L = L;
+  a.P = (L - parity + 1) / 2;
+  a.m = m;
+  a.parity = parity;
+  a.abs_ = abs_;
+  a.cbs = cbs;
+  if (bf16 && m <= 128)
+    return coupled ? lp_dispatch<Bf16x2, true>(a, nb, s) : lp_dispatch<Bf16x2, false>(a, nb, s);
+  if (bf16)
+    return coupled ? lp_dispatch<__nv_bfloat16, true>(a, nb, s)
+                   : lp_dispatch<__nv_bfloat16, false>(a, nb, s);
+  return coupled ? lp_dispatch<float, true>(a, nb, s) : lp_dispatch<float, false>(a, nb, s);
+}
+
+cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,
+                          int nb, Header* hdr, double* s_out, cudaStream_t s) {
+  k_update<<<nb, 256, 0, s>>>(pi, d, out, N, bpart, hdr, s_out);
+  return cudaGetLastError();
+}
+
+}  // namespace mc

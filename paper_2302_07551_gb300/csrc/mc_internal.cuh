@@ -41,6 +41,11 @@ struct Layout {
   int n_planes;
   size_t plane_bytes, vec_bytes;
   size_t off_hdr, off_planes, off_z, off_xa, off_xb, off_wpart, off_dpart, off_rpart, total;
+  // low-precision storage (dtype MC_F32 / MC_BF16)
+  int lp;                // 0: none, 1: FP32, 2: BF16
+  int64_t lp_bs;         // elements per stored block of the A/B planes
+  int64_t lp_cbs;        // floats per block of the FP32 (-T_dd)^{-1} plane
+  size_t off_lpA, off_lpB, off_lpC, off_sc, off_q, off_d, off_bpart;
 };
 
 Layout make_layout(const mc_desc& d);
@@ -76,6 +81,8 @@ struct ResidArgs {
   const double* TLO;
   const double* TDD;
   const double* TUP;
+  const double* NINV;    // with q: (-T_dd)^{-1} plane
+  float* q;              // optional output q = (-T_dd)^{-1} r (FP32)
   const double* x;
   double* rpart;         // one per warp
   Header* hdr;
@@ -96,6 +103,15 @@ cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
 cudaError_t launch_check_scale(const double* x0, double* x, int64_t n, Header* hdr,
                                double* dpart, cudaStream_t s);
+
+cudaError_t launch_lp_convert(const double* src, void* dst, int bf16, float* sc, int sc_stride,
+                              const Layout& lay, int64_t dbs, cudaStream_t s);
+cudaError_t launch_phase_lp(const void* A, const void* B, const float* C, const float* sc,
+                            float* d, const float* q, int64_t L, int m, int parity,
+                            int64_t abs_, int64_t cbs, int bf16, int coupled, int nb,
+                            cudaStream_t s);
+cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,
+                          int nb, Header* hdr, double* s_out, cudaStream_t s);
 
 // Latch an error code into the header (first error wins).
 __device__ __forceinline__ void latch(Header* h, int code) { atomicCAS(&h->status, 0, code); }

@@ -248,8 +248,10 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   }
 }
 
-// Direct residual ||Q^T x||_1 from the stored FP64 blocks (Eq. (1)).
-template <int R>
+// Direct residual ||Q^T x||_1 from the stored FP64 blocks (Eq. (1)).  With
+// WITH_Q the level's residual r_l also yields q_l = (-T_dd)^{-1} r_l, stored
+// in FP32 for the correction sweeps of iterative refinement.
+template <int R, bool WITH_Q>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   extern __shared__ double vsh[];
   __shared__ double sh[32];
@@ -277,6 +279,19 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
 #pragma unroll
     for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));
     wsum += warp_sum(ls);
+    if (WITH_Q) {
+      __syncwarp();
+#pragma unroll
+      for (int r = 0; r < R; ++r) v_lo[lane + 32 * r] = fold<R>(acc[r]);
+      __syncwarp();
+      zero_acc<R>(acc);
+      gemv_acc<R>(acc, a.NINV + (size_t)l * a.ms, v_lo, m, lane);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        if (row < m) a.q[l * m + row] = (float)fold<R>(acc[r]);
+      }
+    }
     __syncwarp();
   }
   if (lane == 0) {
@@ -370,10 +385,16 @@ cudaError_t phase_dispatch(const PhaseArgs& a, int nb, cudaStream_t s) {
 
 template <int R>
 cudaError_t resid_r(const ResidArgs& a, int nb, cudaStream_t s) {
-  static bool done = false;
-  const cudaError_t e = allow_smem(k_residual<R>, vec_smem<R>(), done);
+  static bool done = false, done_q = false;
+  if (a.q) {
+    const cudaError_t e = allow_smem(k_residual<R, true>, vec_smem<R>(), done_q);
+    if (e != cudaSuccess) return e;
+    k_residual<R, true><<<nb, 256, vec_smem<R>(), s>>>(a);
+    return cudaGetLastError();
+  }
+  const cudaError_t e = allow_smem(k_residual<R, false>, vec_smem<R>(), done);
   if (e != cudaSuccess) return e;
-  k_residual<R><<<nb, 256, vec_smem<R>(), s>>>(a);
+  k_residual<R, false><<<nb, 256, vec_smem<R>(), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -38,8 +38,14 @@ def test_workspace_bytes_host_only(lib):
     assert n7 - n5 == 2 * plane
     assert n5 % 256 == 0
     for bad in [(1, 8, 1, 0, 0), (64, 0, 1, 0, 0), (64, 257, 1, 0, 0), (64, 8, 3, 0, 0),
-                (64, 8, 1, 2, 0), (64, 8, 1, 0, 1)]:
+                (64, 8, 1, 2, 0), (64, 8, 1, 0, 3), (64, 6, 1, 0, 1), (64, 10, 1, 0, 2)]:
         assert lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(*bad))) == 0
+    # low-precision storage adds planes and FP32 vectors
+    n64 = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 64, 1, 0, nat.MC_F64)))
+    f32 = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 64, 1, 0, nat.MC_F32)))
+    b16 = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 64, 1, 0, nat.MC_BF16)))
+    assert f32 - b16 == 2 * 64 * 64 * 64 * 2      # two planes at 4 vs 2 bytes per entry
+    assert b16 > n64
     # padded block stride: m = 5 -> 25 doubles padded to 32
     a = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(10, 5, 1, 0, 0)))
     b = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(11, 5, 1, 0, 0)))
