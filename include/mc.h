@@ -236,6 +236,76 @@ int mc_export(mc_chain* chain, int32_t plane, int64_t level0, int64_t count, dou
 int mc_residual_noalloc(const double* dn, const double* loc, const double* up, int64_t L,
                         int32_t m, const double* pi, double* resid_dev, void* cuda_stream);
 
+/* ---------------------------------------------------------------------------
+ * Solve server: continuous batching of many independent chains.  A library
+ * service around the method (the paper solves one chain at a time).
+ *
+ * Requests (generator blocks as for mc_create, but in HOST memory) are
+ * admitted into one caller-owned device arena while their workspace fits
+ * (mc_server_request_bytes each) and at most max_active are running.  Each
+ * mc_server_step runs check_every sweeps (dtype MC_F64) or one refinement
+ * step of check_every correction sweeps (MC_F32 / MC_BF16) for ALL active
+ * requests in shared persistent launches (one per half-sweep and block-size
+ * bucket), then every request's FP64 residual; requests with residual <= tol
+ * (or a latched error, or maxit sweeps) are retired, their pi copied to host
+ * memory and their arena memory freed.  Requests submitted between steps
+ * join the next chunk.  A request's iterates are bitwise independent of the
+ * other requests in the batch and of the launch grid.  With autotune = 1 the
+ * first chunk of every new batch signature times candidate persistent grids
+ * (1-4 resident blocks per SM) on the live requests and keeps the fastest.
+ * --------------------------------------------------------------------------- */
+typedef struct mc_server mc_server;
+
+typedef struct {
+  int32_t dtype;        /* mc_dtype of every request                           */
+  int32_t apply;        /* mc_apply                                            */
+  int32_t stair;        /* 1 or 2                                              */
+  int32_t check_every;  /* sweeps per step (>= 1)                              */
+  double tol;           /* retire when ||Q^T pi||_1 <= tol (tol <= 0: never)    */
+  int64_t maxit;        /* retire (MC_ERR_NO_CONVERGENCE) after this many sweeps */
+  int32_t max_active;   /* 1..1024 requests in flight                          */
+  int32_t autotune;     /* 0 or 1                                              */
+} mc_server_desc;
+
+/*
+ * arena: caller-owned device memory (256-byte aligned) holding the request
+ * table and every admitted request; it must outlive the server.  Syncs no.
+ * Errors: MC_ERR_ARG, MC_ERR_WORKSPACE (arena too small), MC_ERR_CUDA.
+ */
+int mc_server_create(const mc_server_desc* desc, void* arena, size_t arena_bytes,
+                     void* cuda_stream, mc_server** out);
+
+/* Arena bytes one request of L levels and block size m occupies (0 if invalid). */
+size_t mc_server_request_bytes(const mc_server* server, int64_t L, int32_t m);
+
+/*
+ * Admit a request: dn, loc, up are HOST arrays of L blocks of m x m doubles
+ * (row-major, as for mc_create), copied during the call.  tag identifies
+ * the result.  Returns MC_OK, MC_ERR_WORKSPACE when the arena or the slot
+ * count has no room now (retry after a step retires requests), MC_ERR_ARG,
+ * MC_ERR_CUDA.  Low-precision servers need m % 4 == 0.  Start: uniform 1/N.
+ */
+int mc_server_submit(mc_server* server, int64_t tag, int64_t L, int32_t m, const double* dn,
+                     const double* loc, const double* up);
+
+/* One chunk for all active requests (syncs); returns active and finished counts. */
+int mc_server_step(mc_server* server, int32_t* n_active, int32_t* n_done);
+
+/*
+ * Pop the oldest finished request: tag, pi (host, n_cap >= its N; pi_host may
+ * be NULL to discard), result and status (MC_OK, MC_ERR_NO_CONVERGENCE,
+ * MC_ERR_SINGULAR_BLOCK, MC_ERR_BREAKDOWN).  MC_ERR_ARG when none is finished.
+ */
+int mc_server_fetch(mc_server* server, int64_t* tag, double* pi_host, int64_t n_cap,
+                    mc_result* res, int32_t* status);
+
+/* Launch grid in use and the number of tuned batch signatures. */
+int mc_server_grid(const mc_server* server, int32_t* blocks, int32_t* threads,
+                   int32_t* n_tuned);
+
+/* Release the server (requests still active are dropped). */
+void mc_server_destroy(mc_server* server);
+
 /* Wait for the handle's stream and return (and clear) the device status. */
 int mc_sync(mc_chain* chain);
 

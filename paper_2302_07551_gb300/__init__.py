@@ -7,3 +7,4 @@ raises instead of falling back to anything.
 """
 from ._native import McError, PLANES, load  # noqa: F401
 from .chain import Chain, solve  # noqa: F401
+from .server import Server  # noqa: F401

@@ -21,6 +21,13 @@ class McDesc(ctypes.Structure):
                 ("apply", ctypes.c_int32), ("dtype", ctypes.c_int32)]
 
 
+class McServerDesc(ctypes.Structure):
+    _fields_ = [("dtype", ctypes.c_int32), ("apply", ctypes.c_int32), ("stair", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("tol", ctypes.c_double),
+                ("maxit", ctypes.c_int64), ("max_active", ctypes.c_int32),
+                ("autotune", ctypes.c_int32)]
+
+
 class McResult(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int64), ("residual_l1", ctypes.c_double),
                 ("step_l1", ctypes.c_double), ("contraction", ctypes.c_double),
@@ -61,6 +68,22 @@ def load():
     lib.mc_export.restype = ctypes.c_int
     lib.mc_residual_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
     lib.mc_residual_noalloc.restype = ctypes.c_int
+    lib.mc_server_create.argtypes = [ctypes.POINTER(McServerDesc), vp, sz, vp, ctypes.POINTER(vp)]
+    lib.mc_server_create.restype = ctypes.c_int
+    lib.mc_server_request_bytes.argtypes = [vp, i64, i32]
+    lib.mc_server_request_bytes.restype = sz
+    lib.mc_server_submit.argtypes = [vp, i64, i64, i32, vp, vp, vp]
+    lib.mc_server_submit.restype = ctypes.c_int
+    lib.mc_server_step.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+    lib.mc_server_step.restype = ctypes.c_int
+    lib.mc_server_fetch.argtypes = [vp, ctypes.POINTER(i64), vp, i64, ctypes.POINTER(McResult),
+                                    ctypes.POINTER(i32)]
+    lib.mc_server_fetch.restype = ctypes.c_int
+    lib.mc_server_grid.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
+                                   ctypes.POINTER(i32)]
+    lib.mc_server_grid.restype = ctypes.c_int
+    lib.mc_server_destroy.argtypes = [vp]
+    lib.mc_server_destroy.restype = None
     lib.mc_sync.argtypes = [vp]
     lib.mc_sync.restype = ctypes.c_int
     lib.mc_destroy.argtypes = [vp]

@@ -5,24 +5,8 @@
 
 #include <new>
 
-#include "mc_internal.cuh"
+#include "chain.cuh"
 
-struct mc_chain {
-  mc_desc d;
-  mc::Layout lay;
-  char* ws;
-  cudaStream_t user;         // caller's stream: every enqueue goes here
-  cudaStream_t cap;          // private stream used only to capture graphs
-  int num_sms;
-  int factored;
-  int nb_phase, nw;          // persistent sweep grid (blocks, warps)
-  int nb_norm, nb_resid;
-  mc::Header* hdr;           // device header inside the workspace
-  mc::Header* hh;            // pinned host copy of the header
-  double *planes, *z, *xa, *xb, *wpart, *dpart, *rpart;
-  cudaGraphExec_t gexec;     // cached chunk graph of mc_solve
-  int g_chunk, g_resid;
-};
 
 namespace mc {
 
@@ -211,6 +195,16 @@ static int enqueue_refine_step(mc_chain* c, int inner, cudaStream_t s) {
   return enqueue_residual(c, c->xa, s, lpQ(c));
 }
 
+int mc::chain_residual_async(mc_chain* c, const double* x, cudaStream_t s, float* q) {
+  return enqueue_residual(c, x, s, q);
+}
+const void* mc::chain_lpA(mc_chain* c) { return lpA(c); }
+const void* mc::chain_lpB(mc_chain* c) { return lpB(c); }
+const float* mc::chain_lpC(mc_chain* c) { return lpC(c); }
+const float* mc::chain_lpSc(mc_chain* c) { return lpSc(c); }
+float* mc::chain_lpQ(mc_chain* c) { return lpQ(c); }
+float* mc::chain_lpD(mc_chain* c) { return lpD(c); }
+
 // Wait for the stream, fetch the header, clear a latched status.
 static int sync_header(mc_chain* c) {
   CK(cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->user));
@@ -223,19 +217,11 @@ static int sync_header(mc_chain* c) {
   return st;
 }
 
-extern "C" {
-
-size_t mc_workspace_bytes(const mc_desc* desc) {
-  if (!desc_ok(desc)) return 0;
-  return make_layout(*desc).total;
-}
-
-int mc_create(const mc_desc* desc, const double* dn, const double* loc, const double* up,
-              void* workspace, size_t ws_bytes, void* cuda_stream, mc_chain** out) {
+int mc::chain_init(const mc_desc* desc, void* workspace, size_t ws_bytes, cudaStream_t stream,
+                   mc_chain** out) {
   if (!out) return MC_ERR_ARG;
   *out = nullptr;
-  if (!desc_ok(desc) || !dn || !loc || !up) return MC_ERR_ARG;
-  if (((uintptr_t)dn | (uintptr_t)loc | (uintptr_t)up) & 7u) return MC_ERR_ARG;
+  if (!desc_ok(desc)) return MC_ERR_ARG;
   const Layout lay = make_layout(*desc);
   if (!workspace || ((uintptr_t)workspace & 255u) || ws_bytes < lay.total) return MC_ERR_WORKSPACE;
   int dev = 0;
@@ -247,7 +233,7 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   c->d = *desc;
   c->lay = lay;
   c->ws = (char*)workspace;
-  c->user = (cudaStream_t)cuda_stream;
+  c->user = stream;
   c->num_sms = sms;
   c->hdr = (Header*)(c->ws + lay.off_hdr);
   c->planes = (double*)(c->ws + lay.off_planes);
@@ -285,9 +271,7 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   }
   memset(c->hh, 0, sizeof(Header));
   int rc = MC_OK;
-  if (cudaMemsetAsync(c->ws + lay.off_hdr, 0, 4096, c->user) != cudaSuccess ||
-      launch_layout(dn, loc, up, c->planes, lay, c->hdr, c->user) != cudaSuccess)
-    rc = MC_ERR_CUDA;
+  if (cudaMemsetAsync(c->ws + lay.off_hdr, 0, 4096, c->user) != cudaSuccess) rc = MC_ERR_CUDA;
   if (rc != MC_OK) {
     mc_destroy(c);
     return rc;
@@ -296,8 +280,44 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   return MC_OK;
 }
 
+
+extern "C" {
+
+size_t mc_workspace_bytes(const mc_desc* desc) {
+  if (!desc_ok(desc)) return 0;
+  return make_layout(*desc).total;
+}
+
+int mc_create(const mc_desc* desc, const double* dn, const double* loc, const double* up,
+              void* workspace, size_t ws_bytes, void* cuda_stream, mc_chain** out) {
+  if (!out) return MC_ERR_ARG;
+  *out = nullptr;
+  if (!desc_ok(desc) || !dn || !loc || !up) return MC_ERR_ARG;
+  if (((uintptr_t)dn | (uintptr_t)loc | (uintptr_t)up) & 7u) return MC_ERR_ARG;
+  mc_chain* c = nullptr;
+  const int rc = chain_init(desc, workspace, ws_bytes, (cudaStream_t)cuda_stream, &c);
+  if (rc != MC_OK) return rc;
+  if (launch_layout(dn, loc, up, c->planes, c->lay, c->hdr, c->user) != cudaSuccess) {
+    mc_destroy(c);
+    return MC_ERR_CUDA;
+  }
+  *out = c;
+  return MC_OK;
+}
+
 int mc_factor(mc_chain* c) {
   if (!c) return MC_ERR_ARG;
+  const int rc = chain_factor_async(c);
+  if (rc != MC_OK) return rc;
+  const int st = sync_header(c);
+  if (st != MC_OK) return st;
+  c->factored = 1;
+  return MC_OK;
+}
+
+}  // extern "C"
+
+int mc::chain_factor_async(mc_chain* c) {
   c->factored = 0;
   CK(launch_factor(c->planes, c->lay, c->hdr, c->d.apply == MC_APPLY_COUPLED, c->num_sms,
                    c->user));
@@ -313,11 +333,10 @@ int mc_factor(mc_chain* c) {
       CK(launch_lp_convert(c->planes + kPlaneNINV * pe, c->ws + c->lay.off_lpC, 0, nullptr, 0,
                            c->lay, c->lay.lp_cbs, c->user));
   }
-  const int st = sync_header(c);
-  if (st != MC_OK) return st;
-  c->factored = 1;
   return MC_OK;
 }
+
+extern "C" {
 
 int mc_sweep(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, double* stats_dev) {
   if (!c || !x_in || !x_out || nsweeps < 1) return MC_ERR_ARG;

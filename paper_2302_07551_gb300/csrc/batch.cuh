@@ -1,0 +1,73 @@
+// Batched (multi-request) sweep: descriptors shared by batch.cu and server.cu.
+//
+// All active requests of the solve server advance together: one persistent
+// launch per half-sweep covers every level of every request.  The request
+// table lives in device memory and is rewritten by the host between chunks,
+// so one captured CUDA graph serves any active set.  Requests are ordered
+// small blocks first (m <= 128: rows per lane R <= 4) and large blocks after
+// (m <= 256: R = 8); each bucket has its own kernel so that register use
+// follows the bucket.
+//
+// Every reduction is per level first (one partial per level), then per
+// request in level order: a request's iterates do not depend on which other
+// requests share the launch, nor on the grid shape the autotuner picks.
+#pragma once
+#include "mc_internal.cuh"
+
+namespace mc {
+
+constexpr int kMaxReq = 1024;
+
+struct BReq {
+  const double* A;      // FP64 sweep operators: T_lo / W_lo
+  const double* B;      // T_up / W_up
+  const double* C;      // (-T_dd)^{-1} (inverse mode)
+  const double* TLO;    // residual blocks
+  const double* TDD;
+  const double* TUP;
+  const double* NINV;
+  const void* lA;       // low-precision operators (dtype MC_F32 / MC_BF16)
+  const void* lB;
+  const float* lC;
+  const float* sc;
+  float* d;             // correction (low precision)
+  float* q;             // (-T_dd)^{-1} r
+  double* x;            // iterate pi
+  double* z;            // unnormalised sweep output
+  double* xb;           // pi + d before renormalisation
+  double* lsum;         // one partial per level
+  int64_t L;
+  int32_t m, ms, R, p1;  // p1: 0-based parity of the diagonal-only rows
+  int64_t lp_bs, lp_cbs;
+};
+
+struct BTable {
+  int32_t n;            // active requests
+  int32_t n_small;      // requests [0, n_small) have m <= 128
+  int32_t pad[2];
+  int64_t off_h1[kMaxReq + 1];   // prefix counts of half-sweep-1 levels
+  int64_t off_h2[kMaxReq + 1];   // prefix counts of half-sweep-2 levels
+  int64_t off_lv[kMaxReq + 1];   // prefix counts of all levels
+  BReq r[kMaxReq];
+};
+
+struct BOut {
+  double s, step, resid;
+  int32_t status;
+  int32_t pad;
+};
+
+struct BGrid {
+  int blocks, threads;
+};
+
+// One FP64 sweep of every request: both half-sweeps, e^T z, normalisation and
+// step error.  coupled: server-wide apply mode.
+cudaError_t b_sweep(const BTable* t, BOut* out, int coupled, BGrid g, cudaStream_t s);
+// Direct residual of every request's iterate (with_q: also q for refinement).
+cudaError_t b_resid(const BTable* t, BOut* out, int with_q, BGrid g, cudaStream_t s);
+// Mixed precision: d = 0; `inner` correction sweeps; pi <- (pi + d)/e^T(pi + d).
+cudaError_t b_lp_step(const BTable* t, BOut* out, int bf16, int coupled, int inner, BGrid g,
+                      cudaStream_t s);
+
+}  // namespace mc

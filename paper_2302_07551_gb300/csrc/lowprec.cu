@@ -18,88 +18,13 @@
 #include <math.h>
 
 #include "mc_internal.cuh"
+#include "lowprec_dev.cuh"
 
 namespace mc {
 
 namespace {
 
-template <typename T>
-struct Pack;
-template <>
-struct Pack<float> {
-  static constexpr int V = 2;
-  using Raw = float2;
-  __device__ static __forceinline__ Raw load(const float* p) {
-    return __ldcs(reinterpret_cast<const float2*>(p));
-  }
-  __device__ static __forceinline__ Raw zero() { return make_float2(0.0f, 0.0f); }
-  __device__ static __forceinline__ float get(const Raw& r, int e) { return e == 0 ? r.x : r.y; }
-};
-template <>
-struct Pack<__nv_bfloat16> {
-  static constexpr int V = 4;
-  using Raw = uint2;
-  __device__ static __forceinline__ Raw load(const __nv_bfloat16* p) {
-    return __ldcs(reinterpret_cast<const uint2*>(p));
-  }
-  __device__ static __forceinline__ Raw zero() { return make_uint2(0u, 0u); }
-  // bf16 -> fp32 is exact: the 16 bits become the high half of the float
-  __device__ static __forceinline__ float get(const Raw& r, int e) {
-    const unsigned w = (e < 2) ? r.x : r.y;
-    return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
-  }
-};
-
-// BF16 read two rows per lane (4-byte loads), for blocks of at most 128 rows
-// where four-row loads would leave lanes idle.
-struct Bf16x2 {
-  unsigned short bits;   // one bf16, addressed in pairs
-};
-template <>
-struct Pack<Bf16x2> {
-  static constexpr int V = 2;
-  using Raw = unsigned int;
-  __device__ static __forceinline__ Raw load(const Bf16x2* p) {
-    return __ldcs(reinterpret_cast<const unsigned int*>(p));
-  }
-  __device__ static __forceinline__ Raw zero() { return 0u; }
-  __device__ static __forceinline__ float get(const Raw& r, int e) {
-    return __uint_as_float(e ? (r & 0xffff0000u) : (r << 16));
-  }
-};
-
-// acc[g][e] += M(row(g,e), j) * v[j], row(g,e) = 32 V g + V lane + e, for the
-// m columns of a column-major block M of element type T.  U columns per
-// batch so that U * G = 32 packed 8-byte loads per lane are in flight.
-template <typename T, int G>
-__device__ __forceinline__ void gemv_lp(float (&acc)[G][Pack<T>::V], const T* __restrict__ M,
-                                        const float* v, int m, int lane) {
-  constexpr int V = Pack<T>::V, U = (32 / G) < 8 ? 8 : (32 / G);
-  using Raw = typename Pack<T>::Raw;
-  for (int j0 = 0; j0 < m; j0 += U) {
-    Raw t[U][G];
-#pragma unroll
-    for (int q = 0; q < U; ++q)
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int row = 32 * V * g + V * lane;
-        t[q][g] = (j0 + q < m && row < m) ? Pack<T>::load(M + (size_t)(j0 + q) * m + row)
-                                          : Pack<T>::zero();
-      }
-#pragma unroll
-    for (int q = 0; q < U; q += 4) {
-      const float4 vv = *reinterpret_cast<const float4*>(v + j0 + q);
-      const float vq[4] = {vv.x, vv.y, vv.z, vv.w};
-#pragma unroll
-      for (int h = 0; h < 4; ++h)
-#pragma unroll
-        for (int g = 0; g < G; ++g)
-#pragma unroll
-          for (int e = 0; e < V; ++e)
-            acc[g][e] = fmaf(Pack<T>::get(t[q + h][g], e), vq[h], acc[g][e]);
-    }
-  }
-}
+using namespace dev;
 
 struct LpArgs {
   const void* A;       // T_lo or W_lo plane (element type T)
@@ -117,66 +42,17 @@ struct LpArgs {
 template <typename T, int G, int GF, bool COUPLED>
 __global__ void __launch_bounds__(256) k_phase_lp(LpArgs a) {
   extern __shared__ float fsh[];
-  constexpr int V = Pack<T>::V, W = 32 * V * G, WF = 64 * GF;
-  constexpr int SL = (W > WF ? W : WF);
+  constexpr int SL = LpSlice<T, G, GF>::SL;
   const int lane = threadIdx.x & 31;
-  float* v_lo = fsh + (threadIdx.x >> 5) * 3 * SL;
-  float* v_up = v_lo + SL;
-  float* v_g = v_up + SL;
+  float* slice = fsh + (threadIdx.x >> 5) * 3 * SL;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int m = a.m;
   const T* Ap = reinterpret_cast<const T*>(a.A);
   const T* Bp = reinterpret_cast<const T*>(a.B);
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = 2 * u + a.parity;
-    const bool has_lo = l > 0, has_up = l < a.L - 1;
-    const float s_lo = a.sc[2 * l], s_up = a.sc[2 * l + 1];
-    for (int i = lane; i < SL; i += 32) {
-      v_lo[i] = (has_lo && i < m) ? a.d[(l - 1) * m + i] * s_lo : 0.0f;
-      v_up[i] = (has_up && i < m) ? a.d[(l + 1) * m + i] * s_up : 0.0f;
-    }
-    __syncwarp();
-    float acc[G][V];
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-#pragma unroll
-      for (int e = 0; e < V; ++e) acc[g][e] = 0.0f;
-    if (has_lo) gemv_lp<T, G>(acc, Ap + l * a.abs_, v_lo, m, lane);
-    if (has_up) gemv_lp<T, G>(acc, Bp + l * a.abs_, v_up, m, lane);
-    if (COUPLED) {
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int row = 32 * V * g + V * lane;
-        if (row < m)
-#pragma unroll
-          for (int e = 0; e < V; ++e) a.d[l * m + row + e] = acc[g][e] + a.q[l * m + row + e];
-      }
-    } else {
-      for (int i = lane; i < SL; i += 32) v_g[i] = 0.0f;
-      __syncwarp();
-#pragma unroll
-      for (int g = 0; g < G; ++g) {
-        const int row = 32 * V * g + V * lane;
-        if (row < m)
-#pragma unroll
-          for (int e = 0; e < V; ++e) v_g[row + e] = acc[g][e];
-      }
-      __syncwarp();
-      float acc2[GF][2];
-#pragma unroll
-      for (int g = 0; g < GF; ++g) acc2[g][0] = acc2[g][1] = 0.0f;
-      gemv_lp<float, GF>(acc2, a.C + l * a.cbs, v_g, m, lane);
-#pragma unroll
-      for (int g = 0; g < GF; ++g) {
-        const int row = 64 * g + 2 * lane;
-        if (row < m) {
-          a.d[l * m + row] = acc2[g][0] + a.q[l * m + row];
-          a.d[l * m + row + 1] = acc2[g][1] + a.q[l * m + row + 1];
-        }
-      }
-    }
-    __syncwarp();
+    level_sweep_lp<T, G, GF, COUPLED>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_, a.cbs,
+                                      slice, lane);
   }
 }
 
@@ -249,9 +125,7 @@ __global__ void __launch_bounds__(256) k_update(const double* __restrict__ pi,
 
 template <typename T, int G, int GF, bool C>
 cudaError_t lp_launch(const LpArgs& a, int nb, cudaStream_t s) {
-  constexpr int V = Pack<T>::V, W = 32 * V * G, WF = 64 * GF;
-  constexpr int SL = (W > WF ? W : WF);
-  const size_t smem = (size_t)kWarpsPerBlock * 3 * SL * sizeof(float);
+  const size_t smem = (size_t)kWarpsPerBlock * 3 * LpSlice<T, G, GF>::SL * sizeof(float);
   static bool done = false;
   if (!done && smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(

@@ -26,141 +26,27 @@
 #include <math.h>
 
 #include "mc_internal.cuh"
+#include "sweep_dev.cuh"
 
 namespace mc {
 
 namespace {
 
-constexpr unsigned kFull = 0xffffffffu;
-
-__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-  return v;
-}
-
-template <int R>
-struct Tune {
-  static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
-  static constexpr int NA = R <= 2 ? 4 : 2;                            // accumulators per row
-  static constexpr int MINB = R <= 4 ? 3 : 2;                          // blocks per SM
-};
-
-// acc[r][c] += M(row_r, j) * v[j] for the m columns j of a column-major block
-// M; column j feeds accumulator j % NA.  v: per-warp shared slice, zero
-// beyond m (so the pair load at an odd m reads a zero).
-template <int R>
-__device__ __forceinline__ void gemv_acc(double (&acc)[R][Tune<R>::NA],
-                                         const double* __restrict__ M, const double* v, int m,
-                                         int lane) {
-  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
-  for (int j0 = 0; j0 < m; j0 += U) {
-    double t[U][R];
-#pragma unroll
-    for (int q = 0; q < U; ++q) {
-      const int j = j0 + q;
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int row = lane + 32 * r;
-        t[q][r] = (j < m && row < m) ? ld_stream(M + (size_t)j * m + row) : 0.0;
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < U; q += 2) {
-      const double2 vv = *reinterpret_cast<const double2*>(v + j0 + q);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        acc[r][q % NA] = fma(t[q][r], vv.x, acc[r][q % NA]);
-        acc[r][(q + 1) % NA] = fma(t[q + 1][r], vv.y, acc[r][(q + 1) % NA]);
-      }
-    }
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
-                                          int lane) {
-#pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int row = lane + 32 * r;
-    v[row] = row < m ? p[row] : 0.0;
-  }
-}
-
-template <int R>
-__device__ __forceinline__ void zero_acc(double (&acc)[R][Tune<R>::NA]) {
-#pragma unroll
-  for (int r = 0; r < R; ++r)
-#pragma unroll
-    for (int c = 0; c < Tune<R>::NA; ++c) acc[r][c] = 0.0;
-}
-
-template <int R>
-__device__ __forceinline__ double fold(const double (&a)[Tune<R>::NA]) {
-  if constexpr (Tune<R>::NA == 4) {
-    return (a[0] + a[1]) + (a[2] + a[3]);
-  } else {
-    return a[0] + a[1];
-  }
-}
-
-// Deterministic block-wide sum (fixed shuffle tree, fixed warp order).
-__device__ double block_sum(double v, double* sh) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  v = warp_sum(v);
-  __syncthreads();
-  if (lane == 0) sh[w] = v;
-  __syncthreads();
-  double t = lane < nw ? sh[lane] : 0.0;
-  t = warp_sum(t);
-  return t;
-}
+using namespace dev;
 
 template <int R, bool COUPLED>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   extern __shared__ double vsh[];
   __shared__ double red[32];
   __shared__ bool last;
-  constexpr int NA = Tune<R>::NA, W = 32 * R;
   const int lane = threadIdx.x & 31;
-  double* v_lo = vsh + (threadIdx.x >> 5) * 3 * W;
-  double* v_up = v_lo + W;
-  double* v_g = v_up + W;
+  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int m = a.m;
   double wsum = 0.0;
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = 2 * u + a.parity;
-    const bool has_lo = l > 0, has_up = l < a.L - 1;
-    if (has_lo) stage_vec<R>(v_lo, a.src + (l - 1) * m, m, lane);
-    if (has_up) stage_vec<R>(v_up, a.src + (l + 1) * m, m, lane);
-    __syncwarp();
-    double acc[R][NA];
-    zero_acc<R>(acc);
-    if (has_lo) gemv_acc<R>(acc, a.A + (size_t)l * a.ms, v_lo, m, lane);
-    if (has_up) gemv_acc<R>(acc, a.B + (size_t)l * a.ms, v_up, m, lane);
-    if (!COUPLED) {
-#pragma unroll
-      for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
-      __syncwarp();
-      zero_acc<R>(acc);
-      gemv_acc<R>(acc, a.C + (size_t)l * a.ms, v_g, m, lane);
-    }
-    double ls = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-      const int row = lane + 32 * r;
-      const double zr = fold<R>(acc[r]);
-      if (row < m) {
-        a.dst[l * m + row] = zr;
-        ls += zr;
-      }
-    }
-    wsum += warp_sum(ls);
-    __syncwarp();   // the slice is rewritten for the next level
+    wsum += level_sweep<R, COUPLED>(a.A, a.B, a.C, a.src, a.dst, l, a.L, a.m, a.ms, slice, lane);
   }
   if (lane == 0) {
     a.wpart[gw] = wsum;
@@ -256,44 +142,14 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   extern __shared__ double vsh[];
   __shared__ double sh[32];
   __shared__ bool last;
-  constexpr int NA = Tune<R>::NA, W = 32 * R;
   const int lane = threadIdx.x & 31;
-  double* v_lo = vsh + (threadIdx.x >> 5) * 3 * W;
-  double* v_dd = v_lo + W;
-  double* v_up = v_dd + W;
+  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int m = a.m;
   double wsum = 0.0;
-  for (int64_t l = gw; l < a.L; l += nw) {
-    if (l > 0) stage_vec<R>(v_lo, a.x + (l - 1) * m, m, lane);
-    stage_vec<R>(v_dd, a.x + l * m, m, lane);
-    if (l < a.L - 1) stage_vec<R>(v_up, a.x + (l + 1) * m, m, lane);
-    __syncwarp();
-    double acc[R][NA];
-    zero_acc<R>(acc);
-    if (l > 0) gemv_acc<R>(acc, a.TLO + (size_t)l * a.ms, v_lo, m, lane);
-    gemv_acc<R>(acc, a.TDD + (size_t)l * a.ms, v_dd, m, lane);
-    if (l < a.L - 1) gemv_acc<R>(acc, a.TUP + (size_t)l * a.ms, v_up, m, lane);
-    double ls = 0.0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));
-    wsum += warp_sum(ls);
-    if (WITH_Q) {
-      __syncwarp();
-#pragma unroll
-      for (int r = 0; r < R; ++r) v_lo[lane + 32 * r] = fold<R>(acc[r]);
-      __syncwarp();
-      zero_acc<R>(acc);
-      gemv_acc<R>(acc, a.NINV + (size_t)l * a.ms, v_lo, m, lane);
-#pragma unroll
-      for (int r = 0; r < R; ++r) {
-        const int row = lane + 32 * r;
-        if (row < m) a.q[l * m + row] = (float)fold<R>(acc[r]);
-      }
-    }
-    __syncwarp();
-  }
+  for (int64_t l = gw; l < a.L; l += nw)
+    wsum += level_resid<R>(a.TLO, a.TDD, a.TUP, a.NINV, a.x, WITH_Q ? a.q : nullptr, l, a.L, a.m,
+                           a.ms, slice, lane);
   if (lane == 0) {
     a.rpart[gw] = wsum;
     __threadfence();

@@ -1,0 +1,187 @@
+// Device helpers shared by the single-chain and the batched FP64 kernels.
+//
+// Warp-per-level products: lane k owns rows k, k+32, ... (R = ceil(m/32)
+// rows) of a column-major m x m block; input vectors sit in a per-warp
+// shared-memory slice (zero beyond m) and are read as broadcast pairs.
+#pragma once
+#include <math.h>
+
+#include "mc_internal.cuh"
+
+namespace mc {
+namespace dev {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+__device__ __forceinline__ double ld_stream(const double* p) { return __ldcs(p); }
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+template <int R>
+struct Tune {
+  static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
+  static constexpr int NA = R <= 2 ? 4 : 2;                            // accumulators per row
+  static constexpr int MINB = R <= 4 ? 3 : 2;                          // blocks per SM
+};
+
+// acc[r][c] += M(row_r, j) * v[j] for the m columns j of a column-major block
+// M; column j feeds accumulator j % NA.  v: per-warp shared slice, zero
+// beyond m (so the pair load at an odd m reads a zero).
+template <int R>
+__device__ __forceinline__ void gemv_acc(double (&acc)[R][Tune<R>::NA],
+                                         const double* __restrict__ M, const double* v, int m,
+                                         int lane) {
+  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
+  for (int j0 = 0; j0 < m; j0 += U) {
+    double t[U][R];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int j = j0 + q;
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        const int row = lane + 32 * r;
+        t[q][r] = (j < m && row < m) ? ld_stream(M + (size_t)j * m + row) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q += 2) {
+      const double2 vv = *reinterpret_cast<const double2*>(v + j0 + q);
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        acc[r][q % NA] = fma(t[q][r], vv.x, acc[r][q % NA]);
+        acc[r][(q + 1) % NA] = fma(t[q + 1][r], vv.y, acc[r][(q + 1) % NA]);
+      }
+    }
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
+                                          int lane) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = lane + 32 * r;
+    v[row] = row < m ? p[row] : 0.0;
+  }
+}
+
+template <int R>
+__device__ __forceinline__ void zero_acc(double (&acc)[R][Tune<R>::NA]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+#pragma unroll
+    for (int c = 0; c < Tune<R>::NA; ++c) acc[r][c] = 0.0;
+}
+
+template <int R>
+__device__ __forceinline__ double fold(const double (&a)[Tune<R>::NA]) {
+  if constexpr (Tune<R>::NA == 4) {
+    return (a[0] + a[1]) + (a[2] + a[3]);
+  } else {
+    return a[0] + a[1];
+  }
+}
+
+// Deterministic block-wide sum (fixed shuffle tree, fixed warp order).
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  double t = lane < nw ? sh[lane] : 0.0;
+  t = warp_sum(t);
+  return t;
+}
+
+// One level of a half-sweep (Algorithm 2): z_l = (-T_dd)^{-1}(T_lo v_{l-1} +
+// T_up v_{l+1}) (inverse mode: A = T_lo, B = T_up, C = (-T_dd)^{-1}) or
+// z_l = W_lo v_{l-1} + W_up v_{l+1} (coupled: A = W_lo, B = W_up), written to
+// dst; returns sum_i z_l[i] on every lane.  slice: 3 * 32 R doubles of the
+// warp's shared memory.
+template <int R, bool COUPLED>
+__device__ __forceinline__ double level_sweep(const double* A, const double* B, const double* C,
+                                              const double* src, double* dst, int64_t l,
+                                              int64_t L, int m, int ms, double* slice, int lane) {
+  constexpr int NA = Tune<R>::NA, W = 32 * R;
+  double* v_lo = slice;
+  double* v_up = slice + W;
+  double* v_g = slice + 2 * W;
+  const bool has_lo = l > 0, has_up = l < L - 1;
+  if (has_lo) stage_vec<R>(v_lo, src + (l - 1) * m, m, lane);
+  if (has_up) stage_vec<R>(v_up, src + (l + 1) * m, m, lane);
+  __syncwarp();
+  double acc[R][NA];
+  zero_acc<R>(acc);
+  if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
+  if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
+  if (!COUPLED) {
+#pragma unroll
+    for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
+    __syncwarp();
+    zero_acc<R>(acc);
+    gemv_acc<R>(acc, C + (size_t)l * ms, v_g, m, lane);
+  }
+  double ls = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = lane + 32 * r;
+    const double zr = fold<R>(acc[r]);
+    if (row < m) {
+      dst[l * m + row] = zr;
+      ls += zr;
+    }
+  }
+  const double total = warp_sum(ls);
+  __syncwarp();   // the slice is rewritten for the next level
+  return total;
+}
+
+// One level of the direct residual r_l = (Q^T x)_l = T_lo x_{l-1} + T_dd x_l +
+// T_up x_{l+1} (Eq. (1)); returns ||r_l||_1 on every lane.  With q != NULL
+// also stores q_l = (-T_dd)^{-1} r_l in FP32.
+template <int R>
+__device__ __forceinline__ double level_resid(const double* TLO, const double* TDD,
+                                              const double* TUP, const double* NINV,
+                                              const double* x, float* q, int64_t l, int64_t L,
+                                              int m, int ms, double* slice, int lane) {
+  constexpr int NA = Tune<R>::NA, W = 32 * R;
+  double* v_lo = slice;
+  double* v_dd = slice + W;
+  double* v_up = slice + 2 * W;
+  if (l > 0) stage_vec<R>(v_lo, x + (l - 1) * m, m, lane);
+  stage_vec<R>(v_dd, x + l * m, m, lane);
+  if (l < L - 1) stage_vec<R>(v_up, x + (l + 1) * m, m, lane);
+  __syncwarp();
+  double acc[R][NA];
+  zero_acc<R>(acc);
+  if (l > 0) gemv_acc<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+  gemv_acc<R>(acc, TDD + (size_t)l * ms, v_dd, m, lane);
+  if (l < L - 1) gemv_acc<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+  double ls = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));
+  const double total = warp_sum(ls);
+  if (q) {
+    __syncwarp();
+#pragma unroll
+    for (int r = 0; r < R; ++r) v_lo[lane + 32 * r] = fold<R>(acc[r]);
+    __syncwarp();
+    zero_acc<R>(acc);
+    gemv_acc<R>(acc, NINV + (size_t)l * ms, v_lo, m, lane);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      if (row < m) q[l * m + row] = (float)fold<R>(acc[r]);
+    }
+  }
+  __syncwarp();
+  return total;
+}
+
+}  // namespace dev
+}  // namespace mc
