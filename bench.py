@@ -102,6 +102,19 @@ def dist_env():
     return ws, rank, local
 
 
+def aggregate(ms, e2e_s, steps, e2e_steps, ws, device="cpu"):
+    """Whole-job numbers of a multi-rank run: every rank sweeps its own replica
+    (weak scaling, no collective on the data path); the timed region counts as
+    long as the slowest rank.  Returns (ms_max, e2e_s_max, value, e2e_value)."""
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(ms), float(e2e_s)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms, e2e_s = float(t[0]), float(t[1])
+    return ms, e2e_s, ws * steps / (ms * 1e-3), ws * e2e_steps / e2e_s
+
+
 def oracle_sample_rate(name, seconds=15.0, max_levels=4096, threads=0):
     """CPU oracle sweeps/s on a bounded sample (the first levels of the same
     workload), scaled to the full workload's sweeps/s by the level ratio."""
@@ -197,8 +210,10 @@ def run_mine(args):
     del blocks
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)
+    # paired pentadiagonal workloads: skip the structurally zero quadrants
+    paired = synth.WORKLOADS[name]["kind"] == "penta" and args.apply == "inverse" and m % 64 == 0
     with torch.cuda.stream(stream):
-        ch = mcl.Chain(*d, apply=args.apply, stream=stream, dtype=args.dtype)
+        ch = mcl.Chain(*d, apply=args.apply, stream=stream, dtype=args.dtype, paired=paired)
     del d
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -239,9 +254,6 @@ def run_mine(args):
         _, prof = ch.profile(x, y, min(args.steps, 200))
         prof_steps = min(args.steps, 200)
     if ws > 1:
-        t = torch.tensor([ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
         torch.distributed.barrier()
     x, y = y, x
 
@@ -258,10 +270,7 @@ def run_mine(args):
         xh, yh = yh, xh
     e2e_s = time.perf_counter() - t0
     clocks = sampler.stop()
-    if ws > 1:
-        t = torch.tensor([e2e_s], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    ms, e2e_s, value, e2e_value = aggregate(ms, e2e_s, args.steps, ke, ws, device=dev)
 
     # algorithmic bytes and flops (FP64): per level, the stored blocks streamed
     # once (3 m^2 doubles inverse mode, 2 m^2 coupled) plus the neighbour
@@ -269,8 +278,10 @@ def run_mine(args):
     # x and writing pi (16 N bytes) as counted for the whole step.
     nmat = 3 if args.apply == "inverse" else 2
     if args.dtype == "f64":
-        bytes_level = 8 * nmat * m * m + 16 * m
-        sweep_bytes = L * 8 * nmat * m * m + 16 * N
+        # paired chains stream 3/4 of each off-diagonal block
+        mats = (2.5 if paired else nmat)
+        bytes_level = int(8 * mats * m * m) + 16 * m
+        sweep_bytes = L * int(8 * mats * m * m) + 16 * N
         prof_steps = args.steps
     else:
         # FP32 vectors: neighbour d read, q read, d written (16 m bytes / level)
@@ -278,14 +289,13 @@ def run_mine(args):
         mat = 2 * es * m * m + (4 * m * m if args.apply == "inverse" else 0)
         bytes_level = mat + 16 * m
         sweep_bytes = L * bytes_level
-    flops_level = 2 * nmat * m * m
+    flops_level = int(2 * (2.5 if (paired and args.dtype == "f64") else nmat) * m * m)
     half_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * prof_steps)
     half_bytes = bytes_level * L / 2
     half_flops = flops_level * L / 2
     hbm_peak, hbm_src = peaks()
     achieved_gbs = half_bytes / (half_ms * 1e-3) / 1e9
     achieved_tf = half_flops / (half_ms * 1e-3) / 1e12
-    value = ws * args.steps / (ms * 1e-3)
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -324,6 +334,7 @@ def run_mine(args):
         "dtype": "f64" if args.dtype == "f64" else f"{args.dtype} blocks, f32 sweeps, f64 refinement",
         "data": "synthetic (seeded QBD generator, level-dependent blocks)",
         "config": {"workload": name, "L": L, "m": m, "N": N, "apply": args.apply, "stair": 1,
+                   "paired_zero_quadrants_skipped": bool(paired),
                    "block_bytes": sweep_bytes - 16 * N,
                    "refine_every": args.refine_every if args.dtype != "f64" else None,
                    "l2": "no flush: the streamed blocks exceed L2 (129 MB) every step",
@@ -333,7 +344,7 @@ def run_mine(args):
         "kernel_ms_per_sweep": {"half1": prof["half1_ms"] / prof_steps,
                                 "half2": prof["half2_ms"] / prof_steps,
                                 "normalise": prof["norm_ms"] / prof_steps},
-        "e2e": {"value": ws * ke / e2e_s, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N + 8 * 3},
         "gpu_launches": prof["launches"],
         "clocks": clocks,
@@ -386,6 +397,88 @@ def run_solve(args):
                       "results": rows}), flush=True)
 
 
+def run_serve(args):
+    """Continuous-batching serving on the seeded request stream (first K
+    requests): closed-loop capacity, then Poisson arrivals at --load x that
+    capacity; solves/s and p50/p99 latency per form."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2302_07551_gb300 as mcl
+
+    torch.cuda.set_device(0)
+    reqs = synth.request_stream(args.requests)
+    t0 = time.perf_counter()
+    blocks = [synth.qbd(r["L"], r["m"], r["ratio"], r["seed"], True) for r in reqs]
+    gen_s = time.perf_counter() - t0
+    budget = int(args.budget_gb * (1 << 30))
+    forms = {
+        "batched_" + args.serve_dtype: dict(dtype=args.serve_dtype, apply=args.apply,
+                                            max_active=1024, autotune=True),
+        "fp64_one_at_a_time": dict(dtype="f64", apply="inverse", max_active=1, autotune=False),
+    }
+    out = {"mode": "serve", "requests": args.requests, "tol": args.serve_tol,
+           "budget_gb": args.budget_gb, "load": args.load, "check_every": args.refine_every,
+           "stream": "first %d of the seeded stream (L log-uniform [128,16384], m in "
+                     "{16,32,64,128}, ratio U(0.5,0.95))" % args.requests,
+           "host_generation_s": gen_s, "forms": {}}
+    for name, f in forms.items():
+        if args.serve_forms and name.split("_")[0] not in args.serve_forms.split(","):
+            continue
+        srv = mcl.Server(budget, dtype=f["dtype"], apply=f["apply"], tol=args.serve_tol,
+                         check_every=args.refine_every, max_active=f["max_active"],
+                         autotune=f["autotune"])
+
+        def drive(arrivals):
+            """Submit request i once time >= arrivals[i] (and it fits); step
+            until all finish.  Returns per-request (arrival, finish, sweeps)."""
+            start = time.perf_counter()
+            nxt, done, fin = 0, 0, {}
+            queue = []
+            while done < len(reqs):
+                now = time.perf_counter() - start
+                while nxt < len(reqs) and arrivals[nxt] <= now:
+                    queue.append(nxt)
+                    nxt += 1
+                while queue and srv.submit(queue[0], *blocks[queue[0]]):
+                    queue.pop(0)
+                na, _ = srv.step()
+                while True:
+                    r = srv.fetch()
+                    if r is None:
+                        break
+                    tag, _, res, st = r
+                    fin[tag] = (time.perf_counter() - start, res["sweeps"], st, res["residual"])
+                    done += 1
+                if na == 0 and not queue and nxt < len(reqs):
+                    time.sleep(max(0.0, min(arrivals[nxt] - (time.perf_counter() - start), 0.05)))
+            return fin
+
+        fin = drive([0.0] * len(reqs))                 # closed loop: capacity
+        t_cap = max(v[0] for v in fin.values())
+        cap = len(reqs) / t_cap
+        lam = args.load * cap
+        gaps = np.array([r["gap"] for r in reqs]) / lam
+        arr = np.cumsum(gaps) - gaps[0]
+        fin = drive(list(arr))
+        lat = np.array([fin[i][0] - arr[i] for i in range(len(reqs))])
+        span = max(v[0] for v in fin.values()) - arr[0]
+        out["forms"][name] = {
+            "dtype": f["dtype"], "apply": f["apply"], "capacity_solves_s": cap,
+            "arrival_rate": lam, "solves_s": len(reqs) / span,
+            "p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+            "max_s": float(lat.max()), "sweeps_total": int(sum(v[1] for v in fin.values())),
+            "all_converged": all(v[2] == 0 for v in fin.values()),
+            "max_residual": float(np.nanmax([v[3] for v in fin.values()])),
+            "grid": srv.grid(),
+            "per_request": [[i, reqs[i]["L"], reqs[i]["m"], round(reqs[i]["ratio"], 3),
+                             fin[i][1], fin[i][3], round(float(lat[i]), 4), fin[i][2]]
+                            for i in range(len(reqs))]}
+        srv.close()
+    print(json.dumps(out), flush=True)
+
+
 def measure_fp64_peak():
     """FP64 multiply-add peak of this GPU: cuBLAS DGEMM 8192^3, best of 10,
     with the SM clock sampled meanwhile."""
@@ -424,6 +517,13 @@ def main():
     ap.add_argument("--solve", action="store_true",
                     help="time one full solve to --tol per dtype instead of sweeps")
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--serve", action="store_true", help="serving benchmark on the request stream")
+    ap.add_argument("--requests", type=int, default=16)
+    ap.add_argument("--serve-dtype", default="bf16", choices=["f64", "f32", "bf16"])
+    ap.add_argument("--serve-tol", type=float, default=1e-10)
+    ap.add_argument("--serve-forms", default="", help="comma list of form prefixes to run")
+    ap.add_argument("--budget-gb", type=float, default=64.0)
+    ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--measure-fp64-peak", action="store_true")
@@ -437,6 +537,8 @@ def main():
         run_reference(args)
     elif args.solve:
         run_solve(args)
+    elif args.serve:
+        run_serve(args)
     else:
         run_mine(args)
 

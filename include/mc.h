@@ -94,9 +94,18 @@ typedef enum {
 typedef struct {
   int64_t L;       /* number of levels (block rows), L >= 2                     */
   int32_t m;       /* phases per level (block size), 1 <= m <= 256              */
-  int32_t stair;   /* 1: stair matrix of type 1 (default), 2: type 2 (Sect. 2)  */
+  int32_t stair;   /* 1: stair matrix of type 1 (default), 2: type 2 (Sect. 2);
+                      3: block Jacobi, 4: block Gauss-Seidel (the comparison
+                      splittings of Sect. 2; FP64, paired = 0; block Gauss-Seidel
+                      walks the levels in order on one warp, for comparisons)   */
   int32_t apply;   /* mc_apply                                                  */
   int32_t dtype;   /* mc_dtype (MC_F32 / MC_BF16 need m % 4 == 0)               */
+  int32_t paired;  /* 0, or 1: levels are pairs {2J, 2J+1} of a block-pentadiagonal
+                      chain (jumps of +-1, +-2 levels), so the Q^T block (J, J-1) is
+                      zero in rows m/2.. x columns ..m/2 and the block (J, J+1) in
+                      rows ..m/2 x columns m/2..; the FP64 sweep and residual skip
+                      those quadrants.  Needs m % 64 == 0; mc_factor checks that the
+                      quadrants are zero (MC_ERR_ARG otherwise).                 */
 } mc_desc;
 
 typedef struct {

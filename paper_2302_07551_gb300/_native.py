@@ -18,7 +18,7 @@ PLANES = {"tlo": 0, "tup": 1, "tdd": 2, "lu": 3, "ninv": 4, "wlo": 5, "wup": 6}
 
 class McDesc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("m", ctypes.c_int32), ("stair", ctypes.c_int32),
-                ("apply", ctypes.c_int32), ("dtype", ctypes.c_int32)]
+                ("apply", ctypes.c_int32), ("dtype", ctypes.c_int32), ("paired", ctypes.c_int32)]
 
 
 class McServerDesc(ctypes.Structure):

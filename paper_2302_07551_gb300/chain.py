@@ -30,7 +30,7 @@ class Chain:
     """
 
     def __init__(self, dn, loc, up, stair=1, apply="inverse", stream=None, factor=True,
-                 dtype="f64"):
+                 dtype="f64", paired=False):
         lib = nat.load()
         for t, n in ((dn, "dn"), (loc, "loc"), (up, "up")):
             _need(t, loc.shape, n)
@@ -39,7 +39,7 @@ class Chain:
         self.device = loc.device
         self.desc = nat.McDesc(self.L, self.m, int(stair),
                                nat.MC_APPLY_COUPLED if apply == "coupled" else nat.MC_APPLY_INVERSE,
-                               nat.DTYPES[dtype])
+                               nat.DTYPES[dtype], 1 if paired else 0)
         self.dtype = dtype
         self.apply = apply
         nbytes = lib.mc_workspace_bytes(ctypes.byref(self.desc))

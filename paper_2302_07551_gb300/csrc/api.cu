@@ -14,9 +14,11 @@ static size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
 static bool desc_ok(const mc_desc* d) {
   return d && d->L >= 2 && d->L <= (int64_t)1 << 31 && d->m >= 1 && d->m <= kMaxM &&
-         (d->stair == 1 || d->stair == 2) &&
+         (d->stair >= 1 && d->stair <= 4) &&
+         (d->stair <= 2 || (d->dtype == MC_F64 && d->paired == 0)) &&
          (d->apply == MC_APPLY_INVERSE || d->apply == MC_APPLY_COUPLED) &&
-         (d->dtype == MC_F64 || ((d->dtype == MC_F32 || d->dtype == MC_BF16) && d->m % 4 == 0));
+         (d->dtype == MC_F64 || ((d->dtype == MC_F32 || d->dtype == MC_BF16) && d->m % 4 == 0)) &&
+         (d->paired == 0 || (d->paired == 1 && d->m % 64 == 0));
 }
 
 Layout make_layout(const mc_desc& d) {
@@ -81,8 +83,14 @@ using namespace mc;
 
 // Enqueue one sweep.  ev (optional) = 4 events recorded before half-sweep 1,
 // between the half-sweeps, before and after the normalisation.
+// mode: 0 = full sweep (normalise into dst with the step error);
+//       1 = unnormalised (z and e^T z only; dst untouched);
+//       2 = normalise into dst without the step error.
+// scaled_src: src is the unnormalised z of the previous sweep (mode 1), read
+// with the factor 1 / e^T z, which reproduces the stored normalised values.
 static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* stats_out,
-                         cudaStream_t s, cudaEvent_t* ev = nullptr) {
+                         cudaStream_t s, cudaEvent_t* ev = nullptr, int mode = 0,
+                         bool scaled_src = false) {
   const int64_t L = c->lay.L;
   const int p1 = c->d.stair == 1 ? 0 : 1;   // 0-based parity of the diagonal-only rows
   const int p2 = 1 - p1;
@@ -95,6 +103,31 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.L = L;
   a.m = c->lay.m;
   a.ms = c->lay.ms;
+  a.stride = 2;
+  a.s_prev = scaled_src ? &c->hdr->stats[0] : nullptr;
+  if (c->d.stair >= 3) {
+    // comparison splittings of Sect. 2: block Jacobi (every level from x, one
+    // launch) and block Gauss-Seidel (levels in order, one warp)
+    a.src = src;
+    a.src_up = src;
+    a.dst = c->z;
+    a.wpart = c->wpart;
+    a.hdr = c->hdr;
+    a.parity = 0;
+    a.stride = 1;
+    a.P = L;
+    a.reduce_s = 1;
+    a.n_wpart = c->nw;
+    a.paired = 0;
+    if (ev) CK(cudaEventRecord(ev[0], s));
+    if (c->d.stair == 3) {
+      CK(launch_phase(a, coupled, c->nb_phase, s));
+    } else {
+      CK(launch_bgs(a, coupled, s));
+    }
+    if (ev) CK(cudaEventRecord(ev[1], s));
+    if (ev) CK(cudaEventRecord(ev[2], s));
+  } else {
   // half-sweep 1: diagonal-only rows read x at their neighbours
   a.src = src;
   a.dst = c->z;
@@ -104,20 +137,28 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.hdr = c->hdr;
   a.reduce_s = 0;
   a.n_wpart = 2 * c->nw;
+  a.paired = c->d.paired && !coupled;
   if (ev) CK(cudaEventRecord(ev[0], s));
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[1], s));
-  // half-sweep 2: coupled rows read the fresh z of their neighbours
+  // half-sweep 2: coupled rows read the fresh z of their neighbours (this
+  // sweep's own z: never rescaled)
   a.src = c->z;
+  a.s_prev = nullptr;
   a.wpart = c->wpart + c->nw;
   a.parity = p2;
   a.P = (L - p2 + 1) / 2;
   a.reduce_s = 1;   // its last block sums the partials of both half-sweeps
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[2], s));
+  }
+  if (mode == 1) {
+    if (ev) CK(cudaEventRecord(ev[3], s));
+    return MC_OK;
+  }
   NormArgs n{};
   n.z = c->z;
-  n.x_old = src;
+  n.x_old = mode == 0 ? src : nullptr;
   n.x_new = dst;
   n.s = &c->hdr->stats[0];
   n.dpart = c->dpart;
@@ -126,6 +167,31 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   n.N = c->lay.N;
   CK(launch_normalise(n, c->nb_norm, s));
   if (ev) CK(cudaEventRecord(ev[3], s));
+  return MC_OK;
+}
+
+// nsweeps sweeps src -> dst (in place allowed).  Sweeps 1..n-2 stay
+// unnormalised in z (the next sweep scales on read), sweep n-1 writes the
+// normalised iterate to dst, sweep n is a full sweep with the step error:
+// the iterates are bitwise those of n full sweeps, with two normalisation
+// passes instead of n.
+static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
+                          double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr) {
+  const bool lagged = c->d.stair <= 2 && n > 2;
+  for (int64_t k = 0; k < n; ++k) {
+    cudaEvent_t* e = ev ? ev + 4 * k : nullptr;
+    int rc;
+    if (!lagged) {
+      rc = enqueue_sweep(c, k == 0 ? src : dst, dst, k == n - 1 ? stats_out : nullptr, s, e);
+    } else if (k < n - 2) {
+      rc = enqueue_sweep(c, k == 0 ? src : c->z, dst, nullptr, s, e, 1, k > 0);
+    } else if (k == n - 2) {
+      rc = enqueue_sweep(c, c->z, dst, nullptr, s, e, 2, true);
+    } else {
+      rc = enqueue_sweep(c, dst, dst, stats_out, s, e, 0, false);
+    }
+    if (rc != MC_OK) return rc;
+  }
   return MC_OK;
 }
 
@@ -144,6 +210,7 @@ static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float*
   r.L = c->lay.L;
   r.m = c->lay.m;
   r.ms = c->lay.ms;
+  r.paired = c->d.paired;
   CK(launch_residual(r, c->nb_resid, s));
   return MC_OK;
 }
@@ -319,6 +386,11 @@ int mc_factor(mc_chain* c) {
 
 int mc::chain_factor_async(mc_chain* c) {
   c->factored = 0;
+  if (c->d.paired) {
+    const size_t pe = c->lay.plane_bytes / sizeof(double);
+    CK(launch_check_paired(c->planes + kPlaneTLO * pe, c->planes + kPlaneTUP * pe, c->lay, c->hdr,
+                           c->user));
+  }
   CK(launch_factor(c->planes, c->lay, c->hdr, c->d.apply == MC_APPLY_COUPLED, c->num_sms,
                    c->user));
   if (c->lay.lp) {
@@ -342,12 +414,7 @@ int mc_sweep(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, do
   if (!c || !x_in || !x_out || nsweeps < 1) return MC_ERR_ARG;
   if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
-  for (int64_t k = 0; k < nsweeps; ++k) {
-    const int rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out,
-                                 k == nsweeps - 1 ? stats_dev : nullptr, c->user);
-    if (rc != MC_OK) return rc;
-  }
-  return MC_OK;
+  return enqueue_sweeps(c, x_in, x_out, nsweeps, stats_dev, c->user);
 }
 
 int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, double* ms_host) {
@@ -376,8 +443,7 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
       if (rc == MC_OK && cudaEventRecord(ev[4 * k + 3], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
     }
   } else {
-    for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
-      rc = enqueue_sweep(c, k == 0 ? x_in : x_out, x_out, nullptr, c->user, ev + 4 * k);
+    rc = enqueue_sweeps(c, x_in, x_out, nsweeps, nullptr, c->user, ev);
   }
   double t[3] = {0.0, 0.0, 0.0};
   if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
@@ -406,10 +472,8 @@ int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int6
   if (!c->factored) return MC_ERR_NOT_FACTORED;
   const size_t bytes = (size_t)c->lay.N * sizeof(double);
   CK(cudaMemcpyAsync(c->xa, x_in_host, bytes, cudaMemcpyHostToDevice, c->user));
-  for (int64_t k = 0; k < nsweeps; ++k) {
-    const int rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->user);
-    if (rc != MC_OK) return rc;
-  }
+  const int rc = enqueue_sweeps(c, c->xa, c->xa, nsweeps, nullptr, c->user);
+  if (rc != MC_OK) return rc;
   CK(cudaMemcpyAsync(x_out_host, c->xa, bytes, cudaMemcpyDeviceToHost, c->user));
   const int st = sync_header(c);
   if (stats_host) {
@@ -427,7 +491,7 @@ static int capture_chunk(mc_chain* c, int chunk, int with_resid) {
   }
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
   int rc = MC_OK;
-  for (int k = 0; k < chunk && rc == MC_OK; ++k) rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->cap);
+  rc = enqueue_sweeps(c, c->xa, c->xa, chunk, nullptr, c->cap);
   if (rc == MC_OK && with_resid) rc = enqueue_residual(c, c->xa, c->cap);
   if (rc == MC_OK &&
       cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->cap) != cudaSuccess)
@@ -553,8 +617,8 @@ int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, 
       CK(cudaGraphLaunch(c->gexec, c->user));
       CK(cudaStreamSynchronize(c->user));
     } else {
-      for (int64_t q = 0; q < chunk; ++q) {
-        const int rc = enqueue_sweep(c, c->xa, c->xa, nullptr, c->user);
+      {
+        const int rc = enqueue_sweeps(c, c->xa, c->xa, chunk, nullptr, c->user);
         if (rc != MC_OK) return rc;
       }
       if (with_resid) {

@@ -272,7 +272,31 @@ __global__ void __launch_bounds__(256) k_coupled(const double* __restrict__ ninv
   }
 }
 
+// Zero quadrants of a paired pentadiagonal chain (column-major blocks):
+// TLO rows h.. of columns ..h and TUP rows ..h of columns h.., h = m/2.
+__global__ void k_check_paired(const double* __restrict__ tlo, const double* __restrict__ tup,
+                               int64_t L, int m, int ms, Header* hdr) {
+  const int h = m / 2;
+  const int64_t per = (int64_t)h * h;
+  const int64_t total = L * per;
+  bool bad = false;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / per, e = t % per;
+    const int a = (int)(e / h), b = (int)(e % h);   // column a, row b of the quadrant
+    bad |= tlo[(size_t)l * ms + (size_t)a * m + h + b] != 0.0;
+    bad |= tup[(size_t)l * ms + (size_t)(h + a) * m + b] != 0.0;
+  }
+  if (bad) latch(hdr, MC_ERR_ARG);
+}
+
 }  // namespace
+
+cudaError_t launch_check_paired(const double* tlo, const double* tup, const Layout& lay,
+                                Header* hdr, cudaStream_t s) {
+  k_check_paired<<<1024, 256, 0, s>>>(tlo, tup, lay.L, lay.m, lay.ms, hdr);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_layout(const double* dn, const double* loc, const double* up, double* planes,
                           const Layout& lay, Header*, cudaStream_t s) {

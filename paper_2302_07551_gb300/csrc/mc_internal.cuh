@@ -56,19 +56,23 @@ struct PhaseArgs {
   const double* B;       // second operator plane (TUP, or WUP when coupled)
   const double* C;       // NINV plane (inverse mode), unused when coupled
   const double* src;     // vector read at neighbour levels l-1, l+1
+  const double* src_up;  // if set: vector read at level l+1 instead (block Gauss-Seidel)
+  const double* s_prev;  // if set: src is an unnormalised z, scaled by 1 / *s_prev on read
   double* dst;           // z, written at this half-sweep's levels
   double* wpart;         // one level-sum partial per warp
   Header* hdr;
   int64_t L, P;          // levels, levels in this half-sweep
   int m, ms;
-  int parity;            // level of unit u is 2u + parity
+  int parity;            // level of unit u is stride * u + parity
+  int stride;            // 2: stair half-sweep, 1: all levels (block Jacobi)
   int reduce_s;          // last block sums the n_wpart partials into hdr->stats[0]
   int n_wpart;           // partials of both half-sweeps (reduce_s only)
+  int paired;            // skip the zero quadrants of a paired pentadiagonal chain
 };
 
 struct NormArgs {
   const double* z;
-  const double* x_old;
+  const double* x_old;   // NULL: no step error (the previous iterate was not stored)
   double* x_new;
   const double* s;       // e^T z (hdr->stats[0], written by half-sweep 2)
   double* dpart;         // one per block
@@ -89,6 +93,7 @@ struct ResidArgs {
   double* out;           // optional copy of the residual (device)
   int64_t L;
   int m, ms;
+  int paired;
 };
 
 // Launchers (return cudaGetLastError()).
@@ -97,10 +102,16 @@ cudaError_t launch_layout(const double* dn, const double* loc, const double* up,
 cudaError_t launch_factor(double* planes, const Layout& lay, Header* hdr, int coupled,
                           int num_sms, cudaStream_t s);
 cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s);
+// Block Gauss-Seidel step: one warp walks the levels in order (z_{l-1} fresh,
+// x_{l+1} old); e^T z into hdr->stats[0].
+cudaError_t launch_bgs(const PhaseArgs& a, int coupled, cudaStream_t s);
 int phase_blocks_per_sm(int m);   // resident 256-thread blocks of k_phase per SM
 cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
+// Latch MC_ERR_ARG unless the paired zero quadrants of TLO / TUP are zero.
+cudaError_t launch_check_paired(const double* tlo, const double* tup, const Layout& lay,
+                                Header* hdr, cudaStream_t s);
 cudaError_t launch_check_scale(const double* x0, double* x, int64_t n, Header* hdr,
                                double* dpart, cudaStream_t s);
 

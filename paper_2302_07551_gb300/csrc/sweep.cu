@@ -34,7 +34,7 @@ namespace {
 
 using namespace dev;
 
-template <int R, bool COUPLED>
+template <int R, bool COUPLED, bool PAIRED>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   extern __shared__ double vsh[];
   __shared__ double red[32];
@@ -44,9 +44,11 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   double wsum = 0.0;
+  const double scale = a.s_prev ? 1.0 / *a.s_prev : 1.0;
   for (int64_t u = gw; u < a.P; u += nw) {
-    const int64_t l = 2 * u + a.parity;
-    wsum += level_sweep<R, COUPLED>(a.A, a.B, a.C, a.src, a.dst, l, a.L, a.m, a.ms, slice, lane);
+    const int64_t l = a.stride * u + a.parity;
+    wsum += level_sweep<R, COUPLED, PAIRED>(a.A, a.B, a.C, a.src, a.dst, l, a.L, a.m, a.ms, slice,
+                                            lane, scale);
   }
   if (lane == 0) {
     a.wpart[gw] = wsum;
@@ -72,6 +74,21 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   }
 }
 
+// Block Gauss-Seidel (Sect. 2 comparison splitting): M = block lower
+// triangle, so level l needs the new z_{l-1}; one warp walks l = 0..L-1.
+template <int R, bool COUPLED>
+__global__ void __launch_bounds__(32) k_bgs(PhaseArgs a) {
+  __shared__ double slice[3 * 32 * R];
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int64_t l = 0; l < a.L; ++l) {
+    s += level_sweep2<R, COUPLED>(a.A, a.B, a.C, a.dst, a.src_up, a.dst, l, a.L, a.m, a.ms, slice,
+                                  lane);
+    __syncwarp();   // z_l (global, written by all lanes) is read by all lanes next
+  }
+  if (lane == 0) a.hdr->stats[0] = s;
+}
+
 __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   __shared__ double sh[32];
   __shared__ bool last;
@@ -82,7 +99,10 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   double d = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool vec = ((((uintptr_t)a.x_old) | ((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0;
-  if (vec) {
+  if (!a.x_old) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
+      a.x_new[i] = a.z[i] * inv;
+  } else if (vec) {
     const int64_t n2 = a.N / 2;
     const double2* z2 = reinterpret_cast<const double2*>(a.z);
     const double2* x2 = reinterpret_cast<const double2*>(a.x_old);
@@ -137,7 +157,7 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
 // Direct residual ||Q^T x||_1 from the stored FP64 blocks (Eq. (1)).  With
 // WITH_Q the level's residual r_l also yields q_l = (-T_dd)^{-1} r_l, stored
 // in FP32 for the correction sweeps of iterative refinement.
-template <int R, bool WITH_Q>
+template <int R, bool WITH_Q, bool PAIRED>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   extern __shared__ double vsh[];
   __shared__ double sh[32];
@@ -148,8 +168,8 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   double wsum = 0.0;
   for (int64_t l = gw; l < a.L; l += nw)
-    wsum += level_resid<R>(a.TLO, a.TDD, a.TUP, a.NINV, a.x, WITH_Q ? a.q : nullptr, l, a.L, a.m,
-                           a.ms, slice, lane);
+    wsum += level_resid<R, PAIRED>(a.TLO, a.TDD, a.TUP, a.NINV, a.x, WITH_Q ? a.q : nullptr, l,
+                                   a.L, a.m, a.ms, slice, lane);
   if (lane == 0) {
     a.rpart[gw] = wsum;
     __threadfence();
@@ -215,17 +235,26 @@ cudaError_t allow_smem(K kernel, size_t bytes, bool& done) {
   return e;
 }
 
-template <int R, bool C>
+template <int R, bool C, bool P = false>
 cudaError_t phase_r(const PhaseArgs& a, int nb, cudaStream_t s) {
   static bool done = false;
-  const cudaError_t e = allow_smem(k_phase<R, C>, vec_smem<R>(), done);
+  const cudaError_t e = allow_smem(k_phase<R, C, P>, vec_smem<R>(), done);
   if (e != cudaSuccess) return e;
-  k_phase<R, C><<<nb, 256, vec_smem<R>(), s>>>(a);
+  k_phase<R, C, P><<<nb, 256, vec_smem<R>(), s>>>(a);
   return cudaGetLastError();
 }
 
 template <bool C>
 cudaError_t phase_dispatch(const PhaseArgs& a, int nb, cudaStream_t s) {
+  if (a.paired && !C) {
+    switch (a.m / 32) {
+      case 2: return phase_r<2, false, true>(a, nb, s);
+      case 4: return phase_r<4, false, true>(a, nb, s);
+      case 6: return phase_r<6, false, true>(a, nb, s);
+      case 8: return phase_r<8, false, true>(a, nb, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch ((a.m + 31) / 32) {
     case 1: return phase_r<1, C>(a, nb, s);
     case 2: return phase_r<2, C>(a, nb, s);
@@ -239,27 +268,52 @@ cudaError_t phase_dispatch(const PhaseArgs& a, int nb, cudaStream_t s) {
   }
 }
 
-template <int R>
+template <int R, bool P = false>
 cudaError_t resid_r(const ResidArgs& a, int nb, cudaStream_t s) {
   static bool done = false, done_q = false;
   if (a.q) {
-    const cudaError_t e = allow_smem(k_residual<R, true>, vec_smem<R>(), done_q);
+    const cudaError_t e = allow_smem(k_residual<R, true, P>, vec_smem<R>(), done_q);
     if (e != cudaSuccess) return e;
-    k_residual<R, true><<<nb, 256, vec_smem<R>(), s>>>(a);
+    k_residual<R, true, P><<<nb, 256, vec_smem<R>(), s>>>(a);
     return cudaGetLastError();
   }
-  const cudaError_t e = allow_smem(k_residual<R, false>, vec_smem<R>(), done);
+  const cudaError_t e = allow_smem(k_residual<R, false, P>, vec_smem<R>(), done);
   if (e != cudaSuccess) return e;
-  k_residual<R, false><<<nb, 256, vec_smem<R>(), s>>>(a);
+  k_residual<R, false, P><<<nb, 256, vec_smem<R>(), s>>>(a);
   return cudaGetLastError();
 }
 
 }  // namespace
 
+template <int R, bool C>
+cudaError_t bgs_r(const PhaseArgs& a, cudaStream_t s) {
+  k_bgs<R, C><<<1, 32, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool C>
+cudaError_t bgs_dispatch(const PhaseArgs& a, cudaStream_t s) {
+  switch ((a.m + 31) / 32) {
+    case 1: return bgs_r<1, C>(a, s);
+    case 2: return bgs_r<2, C>(a, s);
+    case 3: return bgs_r<3, C>(a, s);
+    case 4: return bgs_r<4, C>(a, s);
+    case 5: return bgs_r<5, C>(a, s);
+    case 6: return bgs_r<6, C>(a, s);
+    case 7: return bgs_r<7, C>(a, s);
+    case 8: return bgs_r<8, C>(a, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 int phase_blocks_per_sm(int m) { return (m + 31) / 32 <= 4 ? 3 : 2; }
 
 cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s) {
   return coupled ? phase_dispatch<true>(a, n_blocks, s) : phase_dispatch<false>(a, n_blocks, s);
+}
+
+cudaError_t launch_bgs(const PhaseArgs& a, int coupled, cudaStream_t s) {
+  return coupled ? bgs_dispatch<true>(a, s) : bgs_dispatch<false>(a, s);
 }
 
 cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s) {
@@ -268,6 +322,15 @@ cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s) {
 }
 
 cudaError_t launch_residual(const ResidArgs& a, int nb, cudaStream_t s) {
+  if (a.paired) {
+    switch (a.m / 32) {
+      case 2: return resid_r<2, true>(a, nb, s);
+      case 4: return resid_r<4, true>(a, nb, s);
+      case 6: return resid_r<6, true>(a, nb, s);
+      case 8: return resid_r<8, true>(a, nb, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch ((a.m + 31) / 32) {
     case 1: return resid_r<1>(a, nb, s);
     case 2: return resid_r<2>(a, nb, s);

@@ -59,13 +59,64 @@ __device__ __forceinline__ void gemv_acc(double (&acc)[R][Tune<R>::NA],
   }
 }
 
+// As gemv_acc, restricted to columns [j0, j1) and row groups r in [R0, R1)
+// (rows lane + 32 r): the structurally nonzero part of a block.
+template <int R, int R0, int R1>
+__device__ __forceinline__ void gemv_acc_part(double (&acc)[R][Tune<R>::NA],
+                                              const double* __restrict__ M, const double* v,
+                                              int j0b, int j1, int m, int lane) {
+  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
+  for (int j0 = j0b; j0 < j1; j0 += U) {
+    double t[U][R1 - R0];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int j = j0 + q;
+#pragma unroll
+      for (int r = R0; r < R1; ++r) {
+        const int row = lane + 32 * r;
+        t[q][r - R0] = (j < j1 && row < m) ? ld_stream(M + (size_t)j * m + row) : 0.0;
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < U; q += 2) {
+      const double2 vv = *reinterpret_cast<const double2*>(v + j0 + q);
+#pragma unroll
+      for (int r = R0; r < R1; ++r) {
+        acc[r][q % NA] = fma(t[q][r - R0], vv.x, acc[r][q % NA]);
+        acc[r][(q + 1) % NA] = fma(t[q + 1][r - R0], vv.y, acc[r][(q + 1) % NA]);
+      }
+    }
+  }
+}
+
+// Products with the off-diagonal Q^T blocks of a paired block-pentadiagonal
+// chain (m = 32 R, R even): T_lo is zero in rows m/2.. of columns ..m/2,
+// T_up in rows ..m/2 of columns m/2..; only the nonzero quadrants are read.
+template <int R>
+__device__ __forceinline__ void gemv_lo_paired(double (&acc)[R][Tune<R>::NA],
+                                               const double* __restrict__ M, const double* v,
+                                               int m, int lane) {
+  gemv_acc_part<R, 0, R / 2>(acc, M, v, 0, m / 2, m, lane);
+  gemv_acc_part<R, 0, R>(acc, M, v, m / 2, m, m, lane);
+}
+template <int R>
+__device__ __forceinline__ void gemv_up_paired(double (&acc)[R][Tune<R>::NA],
+                                               const double* __restrict__ M, const double* v,
+                                               int m, int lane) {
+  gemv_acc_part<R, 0, R>(acc, M, v, 0, m / 2, m, lane);
+  gemv_acc_part<R, R / 2, R>(acc, M, v, m / 2, m, m, lane);
+}
+
+// v = p * scale (scale = 1 / e^T z of the previous sweep when the previous
+// sweep was not normalised in memory; 1 otherwise: fl(z * (1/s)) is exactly
+// the value the normalisation would have stored).
 template <int R>
 __device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
-                                          int lane) {
+                                          int lane, double scale = 1.0) {
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const int row = lane + 32 * r;
-    v[row] = row < m ? p[row] : 0.0;
+    v[row] = row < m ? p[row] * scale : 0.0;
   }
 }
 
@@ -103,22 +154,28 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // z_l = W_lo v_{l-1} + W_up v_{l+1} (coupled: A = W_lo, B = W_up), written to
 // dst; returns sum_i z_l[i] on every lane.  slice: 3 * 32 R doubles of the
 // warp's shared memory.
-template <int R, bool COUPLED>
-__device__ __forceinline__ double level_sweep(const double* A, const double* B, const double* C,
-                                              const double* src, double* dst, int64_t l,
-                                              int64_t L, int m, int ms, double* slice, int lane) {
+template <int R, bool COUPLED, bool PAIRED = false>
+__device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
+                                               const double* src, const double* src_up,
+                                               double* dst, int64_t l, int64_t L, int m, int ms,
+                                               double* slice, int lane, double scale = 1.0) {
   constexpr int NA = Tune<R>::NA, W = 32 * R;
   double* v_lo = slice;
   double* v_up = slice + W;
   double* v_g = slice + 2 * W;
   const bool has_lo = l > 0, has_up = l < L - 1;
-  if (has_lo) stage_vec<R>(v_lo, src + (l - 1) * m, m, lane);
-  if (has_up) stage_vec<R>(v_up, src + (l + 1) * m, m, lane);
+  if (has_lo) stage_vec<R>(v_lo, src + (l - 1) * m, m, lane, scale);
+  if (has_up) stage_vec<R>(v_up, src_up + (l + 1) * m, m, lane, scale);
   __syncwarp();
   double acc[R][NA];
   zero_acc<R>(acc);
-  if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
-  if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
+  if constexpr (PAIRED) {
+    if (has_lo) gemv_lo_paired<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
+    if (has_up) gemv_up_paired<R>(acc, B + (size_t)l * ms, v_up, m, lane);
+  } else {
+    if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
+    if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
+  }
   if (!COUPLED) {
 #pragma unroll
     for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
@@ -141,10 +198,19 @@ __device__ __forceinline__ double level_sweep(const double* A, const double* B, 
   return total;
 }
 
+template <int R, bool COUPLED, bool PAIRED = false>
+__device__ __forceinline__ double level_sweep(const double* A, const double* B, const double* C,
+                                              const double* src, double* dst, int64_t l,
+                                              int64_t L, int m, int ms, double* slice, int lane,
+                                              double scale = 1.0) {
+  return level_sweep2<R, COUPLED, PAIRED>(A, B, C, src, src, dst, l, L, m, ms, slice, lane,
+                                          scale);
+}
+
 // One level of the direct residual r_l = (Q^T x)_l = T_lo x_{l-1} + T_dd x_l +
 // T_up x_{l+1} (Eq. (1)); returns ||r_l||_1 on every lane.  With q != NULL
 // also stores q_l = (-T_dd)^{-1} r_l in FP32.
-template <int R>
+template <int R, bool PAIRED = false>
 __device__ __forceinline__ double level_resid(const double* TLO, const double* TDD,
                                               const double* TUP, const double* NINV,
                                               const double* x, float* q, int64_t l, int64_t L,
@@ -159,9 +225,19 @@ __device__ __forceinline__ double level_resid(const double* TLO, const double* T
   __syncwarp();
   double acc[R][NA];
   zero_acc<R>(acc);
-  if (l > 0) gemv_acc<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+  if (l > 0) {
+    if constexpr (PAIRED)
+      gemv_lo_paired<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+    else
+      gemv_acc<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+  }
   gemv_acc<R>(acc, TDD + (size_t)l * ms, v_dd, m, lane);
-  if (l < L - 1) gemv_acc<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+  if (l < L - 1) {
+    if constexpr (PAIRED)
+      gemv_up_paired<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+    else
+      gemv_acc<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+  }
   double ls = 0.0;
 #pragma unroll
   for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));

@@ -37,9 +37,13 @@ def test_workspace_bytes_host_only(lib):
     plane = 64 * 64 * 8      # m*m = 64 is already a multiple of 32 doubles
     assert n7 - n5 == 2 * plane
     assert n5 % 256 == 0
-    for bad in [(1, 8, 1, 0, 0), (64, 0, 1, 0, 0), (64, 257, 1, 0, 0), (64, 8, 3, 0, 0),
-                (64, 8, 1, 2, 0), (64, 8, 1, 0, 3), (64, 6, 1, 0, 1), (64, 10, 1, 0, 2)]:
+    for bad in [(1, 8, 1, 0, 0), (64, 0, 1, 0, 0), (64, 257, 1, 0, 0), (64, 8, 5, 0, 0),
+                (64, 8, 1, 2, 0), (64, 8, 1, 0, 3), (64, 6, 1, 0, 1), (64, 10, 1, 0, 2),
+                (64, 8, 3, 0, 1), (64, 32, 1, 0, 0, 1), (64, 64, 4, 0, 0, 1), (64, 64, 1, 0, 0, 2)]:
         assert lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(*bad))) == 0
+    # comparison splittings and paired chains
+    assert lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 8, 3, 0, 0))) > 0
+    assert lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 128, 1, 0, 0, 1))) > 0
     # low-precision storage adds planes and FP32 vectors
     n64 = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 64, 1, 0, nat.MC_F64)))
     f32 = lib.mc_workspace_bytes(ctypes.byref(nat.McDesc(64, 64, 1, 0, nat.MC_F32)))

@@ -226,3 +226,93 @@ def test_full_size_qbd_L32768_m64_sampled():
     # and e^T x = 1, x >= 0 at full size
     assert abs(xk1.sum() - 1) <= 1e-12 and (xk1 >= 0).all()
     ch.close()
+
+
+# --- paired block-pentadiagonal chains: zero quadrants skipped ------------------------
+
+@pytest.mark.parametrize("Lp,mp", [(12, 32), (10, 64), (8, 128), (9, 96)])
+def test_paired_pentadiagonal_skips_zero_quadrants(Lp, mp):
+    """Levels of a chain with jumps of +-1, +-2 paired into blocks of 2 mp:
+    the sweep that skips the structurally zero quadrants equals the oracle's
+    dense sweep, as does the residual."""
+    if Lp % 2:
+        Lp += 1
+    blocks = synth.penta_paired(Lp, mp, 0.8, 0.3, seed=Lp + mp)
+    oc = oracle.Chain(*blocks)
+    L, m = Lp // 2, 2 * mp
+    if m % 64:
+        with pytest.raises(ValueError):
+            mc.Chain(*(dev(b) for b in blocks), paired=True)
+        return
+    ch = mc.Chain(*(dev(b) for b in blocks), paired=True)
+    N = L * m
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    x = ch.sweep(x0, nsweeps=30).cpu().numpy()
+    ref = oc.sweeps(np.full(N, 1.0 / N), 30)
+    assert rel_l1(x, ref) <= 1e-12
+    y = np.random.default_rng(1).random(N)
+    assert abs(ch.residual(dev(y)) - oc.residual(y)) <= 1e-12 * oc.residual(y)
+    pi, res = ch.solve(tol=1e-12, maxit=200000, check_every=32)
+    sol = oc.solve(tol=1e-13, maxit=200000, check_every=32)["x"]
+    assert rel_l1(pi.cpu().numpy(), sol) <= 1e-10
+    ch.close()
+
+
+def test_paired_flag_rejects_dense_off_diagonal_blocks():
+    blocks = synth.qbd(6, 64, 0.8, seed=3)
+    with pytest.raises(mc.McError) as e:
+        mc.Chain(*(dev(b) for b in blocks), paired=True)
+    assert e.value.status == 1
+
+
+# --- comparison splittings of Sect. 2 on the GPU --------------------------------------
+
+@pytest.mark.parametrize("stair,meth", [(3, oracle.BJ), (4, oracle.BGS)])
+@pytest.mark.parametrize("L,m", [(37, 5), (64, 64), (9, 160)])
+def test_block_jacobi_and_gauss_seidel_sweeps(stair, meth, L, m):
+    K = 20
+    blocks, oc = make(L, m, seed=L + 7 * m)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=stair)
+    N = L * m
+    x = ch.sweep(torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda"), nsweeps=K)
+    ref = oc.sweeps(np.full(N, 1.0 / N), K, method=meth)
+    assert rel_l1(x.cpu().numpy(), ref) <= 1e-12
+    ch.close()
+
+
+def test_contraction_stair_equals_gauss_seidel_and_jacobi_stalls():
+    """Sect. 2: on block-tridiagonal Q^T the staircase iteration converges at
+    the block Gauss-Seidel rate; block Jacobi has |lambda| = 1 twice."""
+    blocks = synth.workload("qbd_L64_m8")
+    kap = {}
+    for stair in (1, 2, 4):
+        ch = mc.Chain(*(dev(b) for b in blocks), stair=stair)
+        _, res = ch.solve(tol=0.0, eps=1e-13, maxit=20000, check_every=100)
+        kap[stair] = res["contraction"]
+        ch.close()
+    assert abs(kap[1] - kap[4]) < 2e-3 and abs(kap[2] - kap[4]) < 2e-3
+    gamma = sorted(abs(np.linalg.eigvals(oracle.Chain(*blocks).iteration_matrix(oracle.BGS))))[-2]
+    assert abs(kap[1] - gamma) < 2e-3
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=3)
+    _, res = ch.solve(tol=0.0, eps=1e-13, maxit=2000, check_every=100, raise_on_maxit=False)
+    assert res["status"] == 7 and res["step"] > 1e-6     # block Jacobi does not converge
+    ch.close()
+
+
+def test_multi_sweep_call_equals_single_sweeps_bitwise():
+    """n sweeps in one call (normalisation applied on read between sweeps) are
+    bitwise the n single sweeps, including e^T z and the step error."""
+    blocks, _ = make(45, 24, seed=8)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    N = 45 * 24
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    for n in (2, 3, 7):
+        st_a = torch.zeros(3, dtype=torch.float64, device="cuda")
+        st_b = torch.zeros(3, dtype=torch.float64, device="cuda")
+        a = ch.sweep(x0, nsweeps=n, stats=st_a)
+        b = x0.clone()
+        for _ in range(n):
+            b = ch.sweep(b, nsweeps=1, stats=st_b)
+        assert torch.equal(a, b)
+        assert torch.equal(st_a[:2], st_b[:2])
+    ch.close()

@@ -1,0 +1,68 @@
+"""Multi-rank bench logic on CPU with gloo (world size 2): replicas with no
+data-path collective, max-over-ranks timing and whole-job throughput; the
+reference arm prints on rank 0 only."""
+import os
+import socket
+import sys
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as tmp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, port, q):
+    sys.path.insert(0, ROOT)
+    import bench
+    dist.init_process_group("gloo", init_method=f"tcp://127.0.0.1:{port}", rank=rank,
+                            world_size=2)
+    ms = [10.0, 12.5][rank]          # rank 1 is the slower replica
+    e2e = [2.0, 1.5][rank]
+    out = bench.aggregate(ms, e2e, steps=100, e2e_steps=50, ws=2)
+    q.put((rank, out))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_aggregate_takes_the_slowest_rank():
+    ctx = tmp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = dict(q.get(timeout=120) for _ in range(2))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    for r in range(2):
+        ms, e2e_s, value, e2e_value = res[r]
+        assert ms == 12.5 and e2e_s == 2.0
+        assert value == pytest.approx(2 * 100 / 12.5e-3)
+        assert e2e_value == pytest.approx(2 * 50 / 2.0)
+
+
+def test_single_rank_aggregate_is_local():
+    sys.path.insert(0, ROOT)
+    import bench
+    ms, e2e_s, value, e2e_value = bench.aggregate(4.0, 1.0, 10, 5, 1)
+    assert (ms, e2e_s) == (4.0, 1.0) and value == pytest.approx(2500.0) and e2e_value == 5.0
+
+
+def test_reference_arm_silent_on_other_ranks(monkeypatch, capsys):
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("RANK", "1")
+
+    class A:
+        workload, steps, warmup = "qbd_L64_m8", 3, 3
+    bench.run_reference(A())
+    assert capsys.readouterr().out == ""
