@@ -310,11 +310,14 @@ def run_mine(args):
         import hashlib
         with open(tp) as f:
             tj = json.load(f)
-        with open(os.path.join(ROOT, "paper_2302_07551_gb300", "csrc", "sweep.cu"), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+        hs = hashlib.sha256()
+        for src in ("sweep.cu", "sweep_dev.cuh"):
+            with open(os.path.join(ROOT, "paper_2302_07551_gb300", "csrc", src), "rb") as f:
+                hs.update(f.read())
+        sha = hs.hexdigest()[:16]
         key = f"{name}:{args.apply}"
         # counters taken on an older kernel source do not describe this one
-        if key in tj and tj.get("sweep_cu_sha256") == sha:
+        if args.dtype == "f64" and key in tj and tj.get("kernel_src_sha256") == sha:
             traffic = tj[key]["bytes_per_launch"]
     if args.dtype == "f64":
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,

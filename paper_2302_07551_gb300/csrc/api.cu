@@ -462,7 +462,11 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   ms_host[0] = t[0];
   ms_host[1] = t[1];
   ms_host[2] = t[2];
-  ms_host[3] = 3.0 * (double)nsweeps;
+  // kernel launches: 2 per sweep (1 for the comparison splittings) plus the
+  // normalisations (1 per sweep unless the lagged scheme keeps them to 2)
+  const bool lagged = !c->lay.lp && c->d.stair <= 2 && nsweeps > 2;
+  const double per = c->lay.lp ? 2.0 : (c->d.stair <= 2 ? 2.0 : 1.0);
+  ms_host[3] = per * (double)nsweeps + (c->lay.lp ? 1.0 : (lagged ? 2.0 : (double)nsweeps));
   return sync_header(c);
 }
 

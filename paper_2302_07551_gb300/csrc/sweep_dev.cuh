@@ -65,7 +65,8 @@ template <int R, int R0, int R1>
 __device__ __forceinline__ void gemv_acc_part(double (&acc)[R][Tune<R>::NA],
                                               const double* __restrict__ M, const double* v,
                                               int j0b, int j1, int m, int lane) {
-  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
+  // batch size follows the rows actually read (about 16 loads in flight)
+  constexpr int U = Tune<R1 - R0>::U, NA = Tune<R>::NA;
   for (int j0 = j0b; j0 < j1; j0 += U) {
     double t[U][R1 - R0];
 #pragma unroll
