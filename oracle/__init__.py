@@ -70,6 +70,10 @@ def _load():
     lib.or_sweep_rhs.restype = i32
     lib.or_residual_vec.argtypes = [i64, i32, vp, vp, vp, vp, vp]
     lib.or_residual_vec.restype = None
+    lib.or_sweep_banded.argtypes = [i64, i32, i32, vp, vp, vp, vp, i32, vp, vp]
+    lib.or_sweep_banded.restype = i32
+    lib.or_residual_banded.argtypes = [i64, i32, i32, vp, vp, vp]
+    lib.or_residual_banded.restype = dbl
     lib.or_threads.argtypes = [i32]
     lib.or_threads.restype = i32
     _lib = lib
@@ -213,3 +217,77 @@ def contraction(err_hist, window=50):
     d = np.asarray(err_hist)
     w = min(window, len(d) - 1)
     return float((d[-1] / d[-1 - w]) ** (1.0 / w))
+
+
+class BandedChain:
+    """Block-banded T = Q^T from generator block diagonals (Algorithm 2 in full).
+
+    diags: dict {e: array (L, m, m)} with diags[e][l] = Q[l, l+e] (row-major),
+    e in [-p, q] including 0 (entries whose level l+e is outside [0, L) are
+    ignored).  T blocks: T[l, l+d] = (Q[l+d, l])^T = (diags[-d][l+d])^T.
+    """
+
+    def __init__(self, diags):
+        es = sorted(diags)
+        L, m, _ = diags[0].shape
+        self.L, self.m, self.N = L, m, L * m
+        self.off = np.array(sorted(-e for e in es), dtype=np.int32)
+        nd = len(self.off)
+        self.TB = np.zeros((nd, L, m, m))
+        for j, d in enumerate(self.off):
+            G = _c64(diags[-int(d)])
+            for l in range(L):
+                k = l + int(d)
+                if 0 <= k < L:
+                    self.TB[j, l] = G[k].T
+        jd = int(np.nonzero(self.off == 0)[0][0])
+        self.Tdd = np.ascontiguousarray(self.TB[jd])
+        self.LU = np.empty_like(self.Tdd)
+        self.piv = np.empty((L, m), np.int32)
+        self.swaps = _load().or_factor(L, m, _p(self.Tdd), _p(self.LU), _p(self.piv))
+        if self.swaps < 0:
+            raise ValueError("singular diagonal block")
+
+    def sweep(self, x, method=STAIR1):
+        x = _c64(x).reshape(-1)
+        z = np.empty(self.N)
+        rc = _load().or_sweep_banded(self.L, self.m, len(self.off), _p(self.off), _p(self.TB),
+                                     _p(self.LU), _p(self.piv), int(method), _p(x), _p(z))
+        if rc != 0:
+            raise ValueError("bad method")
+        return z
+
+    def sweeps(self, x, k, method=STAIR1):
+        x = _c64(x).reshape(-1).copy()
+        for _ in range(k):
+            z = self.sweep(x, method)
+            x = z / _seqsum(z)
+        return x
+
+    def residual(self, x):
+        x = _c64(x).reshape(-1)
+        return _load().or_residual_banded(self.L, self.m, len(self.off), _p(self.off),
+                                          _p(self.TB), _p(x))
+
+    def solve(self, tol=1e-12, maxit=100000, check_every=1, method=STAIR1):
+        x = np.full(self.N, 1.0 / self.N)
+        k = 0
+        r = self.residual(x)
+        while k < maxit and not r <= tol:
+            for _ in range(check_every):
+                z = self.sweep(x, method)
+                x = z / _seqsum(z)
+                k += 1
+            r = self.residual(x)
+        return dict(x=x, sweeps=k, resid=r)
+
+    def dense_T(self):
+        L, m = self.L, self.m
+        T = np.zeros((self.N, self.N))
+        for j, d in enumerate(self.off):
+            for l in range(L):
+                k = l + int(d)
+                if 0 <= k < L:
+                    T[l * m:(l + 1) * m, k * m:(k + 1) * m] = self.TB[j, l]
+        return T
+

@@ -336,3 +336,102 @@ int or_threads(int n) {
   return 1;
 #endif
 }
+
+/*
+ * Block-banded T = Q^T (Sect. 2 block partition, Algorithm 2 in full): nd
+ * block diagonals with offsets off[0..nd) (T_{l, l+off[j]}), blocks row-major
+ * in TB[j][l] (zero where l+off[j] is outside [0, L)); the diagonal offset 0
+ * must be present (index jd).  One unnormalised step z = M^{-1} N x:
+ *   stair types: step 1 z_i = -sum_{k not in J_i, k != i} Q_{i,k} x_k,
+ *     J_i = {i} on diagonal-only rows and {i-1, i+1} on coupled rows;
+ *     step 2 diagonal-only rows z_i = Q_ii^{-1} z_i;
+ *     step 3 coupled rows z_i = Q_ii^{-1}(z_i - Q_{i,i-1} z_{i-1} - Q_{i,i+1} z_{i+1});
+ *   BGS: z_l = Q_ll^{-1}(- sum_{d<0} Q_{l,l+d} z_{l+d} - sum_{d>0} Q_{l,l+d} x_{l+d});
+ *   BJ:  z_l = Q_ll^{-1}(- sum_{d!=0} Q_{l,l+d} x_{l+d}).
+ * Returns 0, or -1 on a bad method / missing diagonal.
+ */
+int or_sweep_banded(int64_t L, int m, int nd, const int* off, const double* TB, const double* LU,
+                    const int* piv, int method, const double* x, double* z) {
+  int jd = -1;
+  for (int j = 0; j < nd; ++j) if (off[j] == 0) jd = j;
+  if (jd < 0) return -1;
+  (void)jd;
+  const size_t mm = (size_t)m * m;
+#define TBLK(j, l) (TB + ((size_t)(j) * (size_t)L + (size_t)(l)) * mm)
+  if (method == OR_STAIR1 || method == OR_STAIR2) {
+    const int type = method == OR_STAIR1 ? 1 : 2;
+#pragma omp parallel for
+    for (int64_t l = 0; l < L; ++l) {          /* step 1 */
+      double* acc = (double*)calloc((size_t)m, sizeof(double));
+      const int diag_only = stair_diag_only(type, l);
+      for (int j = 0; j < nd; ++j) {
+        const int d = off[j];
+        if (d == 0) continue;
+        if (!diag_only && (d == -1 || d == 1)) continue;   /* in J_i */
+        const int64_t k = l + d;
+        if (k < 0 || k >= L) continue;
+        gemv_acc(m, TBLK(j, l), x + (size_t)k * m, acc);
+      }
+      for (int i = 0; i < m; ++i) z[(size_t)l * m + i] = -acc[i];
+      free(acc);
+    }
+#pragma omp parallel for
+    for (int64_t l = 0; l < L; ++l)            /* step 2 */
+      if (stair_diag_only(type, l))
+        or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, z + (size_t)l * m);
+#pragma omp parallel for
+    for (int64_t l = 0; l < L; ++l)            /* step 3 */
+      if (!stair_diag_only(type, l)) {
+        double* acc = (double*)calloc((size_t)m, sizeof(double));
+        for (int j = 0; j < nd; ++j) {
+          const int d = off[j];
+          if (d != -1 && d != 1) continue;
+          const int64_t k = l + d;
+          if (k < 0 || k >= L) continue;
+          gemv_acc(m, TBLK(j, l), z + (size_t)k * m, acc);
+        }
+        for (int i = 0; i < m; ++i) z[(size_t)l * m + i] -= acc[i];
+        free(acc);
+        or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, z + (size_t)l * m);
+      }
+    return 0;
+  }
+  if (method == OR_BGS || method == OR_BJ) {
+    for (int64_t l = 0; l < L; ++l) {
+      double* acc = (double*)calloc((size_t)m, sizeof(double));
+      for (int j = 0; j < nd; ++j) {
+        const int d = off[j];
+        if (d == 0) continue;
+        const int64_t k = l + d;
+        if (k < 0 || k >= L) continue;
+        const double* v = (method == OR_BGS && d < 0) ? z : x;
+        gemv_acc(m, TBLK(j, l), v + (size_t)k * m, acc);
+      }
+      for (int i = 0; i < m; ++i) z[(size_t)l * m + i] = -acc[i];
+      free(acc);
+      or_lu_solve(m, BLK(LU, l, m), piv + (size_t)l * m, z + (size_t)l * m);
+    }
+    return 0;
+  }
+#undef TBLK
+  return -1;
+}
+
+/* ||T x||_1 for block-banded T (Eq. (1)). */
+double or_residual_banded(int64_t L, int m, int nd, const int* off, const double* TB,
+                          const double* x) {
+  const size_t mm = (size_t)m * m;
+  double r = 0.0;
+  double* acc = (double*)malloc(sizeof(double) * (size_t)m);
+  for (int64_t l = 0; l < L; ++l) {
+    for (int i = 0; i < m; ++i) acc[i] = 0.0;
+    for (int j = 0; j < nd; ++j) {
+      const int64_t k = l + off[j];
+      if (k < 0 || k >= L) continue;
+      gemv_acc(m, TB + ((size_t)j * (size_t)L + (size_t)l) * mm, x + (size_t)k * m, acc);
+    }
+    for (int i = 0; i < m; ++i) r += fabs(acc[i]);
+  }
+  free(acc);
+  return r;
+}

@@ -32,6 +32,10 @@ WORKLOADS = {
     "qbd_L32768_m64": dict(kind="qbd", L=32768, m=64, ratio=0.9, level_dependent=True, seed=1),
     # same recipe at L=8192 (0.8 GB of blocks per sweep): profiling-size case
     "qbd_L8192_m64": dict(kind="qbd", L=8192, m=64, ratio=0.9, level_dependent=True, seed=1),
+    # block Hessenberg: batch arrivals of up to 4 levels, single-level service;
+    # L=4096, m=64, level-dependent, up/down rate ratio 0.8, jump rates halve per level
+    "hessenberg_L4096_m64": dict(kind="banded", L=4096, m=64, p=1, q=4, ratio=0.8, decay=0.5,
+                                 seed=5),
     # jumps +-1, +-2 on L=8192 levels of m=128, paired to 4096 levels of 256
     "penta_L8192_m128": dict(kind="penta", L=8192, m=128, ratio=0.8, scale2=0.3, seed=2),
     # same recipe at L=1024 (time-to-solution comparisons)
@@ -68,6 +72,8 @@ def _load():
     lib.synth_penta_levels.restype = i32
     lib.synth_penta_levels.argtypes = [u64, u64, i64, i32, dbl, dbl, i64, i64, vp, vp, vp]
     lib.synth_qbd_first_irreducible.restype = i32
+    lib.synth_banded_levels.restype = i32
+    lib.synth_banded_levels.argtypes = [u64, i64, i32, i32, i32, dbl, dbl, i32, i64, i64, vp]
     lib.synth_qbd_first_irreducible.argtypes = [u64, i64, i32, i32, vp, vp, vp]
     _lib = lib
     return lib
@@ -134,6 +140,19 @@ def penta_paired(L, m, ratio, scale2, seed, J0=0, J1=None, out=None):
     return dn, loc, up
 
 
+def banded(L, m, p, q, ratio, seed, decay=0.5, level_dependent=True, l0=0, l1=None):
+    """Block-banded generator with jumps of -p..q levels (block Hessenberg for
+    p == 1 or q == 1): dict {e: (l1-l0, m, m) array of Q[l, l+e]}."""
+    l1 = L if l1 is None else l1
+    n = l1 - l0
+    out = np.empty((p + q + 1, n, m, m), np.float64)
+    rc = _load().synth_banded_levels(seed, L, m, p, q, float(ratio), float(decay),
+                                     int(level_dependent), l0, l1, _ptr(out))
+    if rc != 0:
+        raise ValueError("synth_banded_levels: bad arguments")
+    return {e: out[e + p] for e in range(-p, q + 1)}
+
+
 def birth_death(L, lam, mu):
     """m = 1 birth-death generator: up-rate lam, down-rate mu."""
     dn = np.zeros((L, 1, 1))
@@ -152,6 +171,9 @@ def workload(name, l0=0, l1=None):
         return qbd(w["L"], w["m"], w["ratio"], w["seed"], w["level_dependent"], l0, l1)
     if w["kind"] == "penta":
         return penta_paired(w["L"], w["m"], w["ratio"], w["scale2"], w["seed"], l0, l1)
+    if w["kind"] == "banded":
+        return banded(w["L"], w["m"], w["p"], w["q"], w["ratio"], w["seed"], w["decay"], True,
+                      l0, l1 if l1 is not None else w["L"])
     if w["kind"] == "birth_death":
         dn, loc, up = birth_death(w["L"], w["lam"], w["mu"])
         l1 = w["L"] if l1 is None else l1

@@ -246,3 +246,64 @@ int synth_qbd_first_irreducible(uint64_t seed, int64_t L, int m, int level_depen
   }
   return -1;
 }
+
+/*
+ * Block-banded generator: jumps of e levels for e in [-p, q] \ {0}, m phases.
+ * Per level l (key = l if level_dependent else 0) and jump e: block A_e with
+ * entries nonzero w.p. 1/2 (diagonal forced positive for e = +-1), values
+ * Uniform(0.1, 1) times decay^(|e|-1); A1 local with zero diagonal.  All down
+ * blocks (e < 0) are then multiplied by one factor so that the level's total
+ * up-rate / total down-rate = ratio (sums over all entries, before dropping
+ * the jumps that leave [0, L-1]).  Diagonal of Q_{l,l} = -(row sums of the
+ * retained blocks, in the order e = -p..q, local at e = 0).
+ * out[(e + p) * (l1-l0) + (l - l0)] = Q_{l, l+e} (row-major m x m), e = 0 the
+ * local block with its diagonal.  Returns 0 or -1 on bad arguments.
+ */
+int synth_banded_levels(uint64_t seed, int64_t L, int m, int p, int q, double ratio, double decay,
+                        int level_dependent, int64_t l0, int64_t l1, double* out) {
+  if (L < 1 || m < 1 || p < 1 || q < 1 || p > 16 || q > 16 || l0 < 0 || l1 > L || l0 > l1 ||
+      !(ratio > 0) || !(decay > 0))
+    return -1;
+  const size_t mm = (size_t)m * m, nl = (size_t)(l1 - l0);
+#pragma omp parallel for schedule(dynamic, 4)
+  for (int64_t l = l0; l < l1; ++l) {
+    const uint64_t lk = level_dependent ? (uint64_t)l : 0u;
+    double su = 0.0, sd = 0.0;
+    for (int e = -p; e <= q; ++e) {
+      double* B = out + ((size_t)(e + p) * nl + (size_t)(l - l0)) * mm;
+      if (e == 0) {
+        fill_rate_block(B, m, seed, 0, lk, K_A1, 0, 1);
+        continue;
+      }
+      const uint64_t kind = 16 + (uint64_t)(e + 16);
+      fill_rate_block(B, m, seed, 0, lk, kind, e == 1 || e == -1, 0);
+      double w = 1.0;
+      for (int k = 1; k < (e > 0 ? e : -e); ++k) w *= decay;
+      for (size_t t = 0; t < mm; ++t) B[t] = B[t] * w;
+      if (e > 0) su += block_sum(B, m); else sd += block_sum(B, m);
+    }
+    const double c = su / (ratio * sd);
+    for (int e = -p; e < 0; ++e) {
+      double* B = out + ((size_t)(e + p) * nl + (size_t)(l - l0)) * mm;
+      for (size_t t = 0; t < mm; ++t) B[t] = B[t] * c;
+    }
+    for (int e = -p; e <= q; ++e) {
+      if (e == 0) continue;
+      if (l + e < 0 || l + e > L - 1) {
+        double* B = out + ((size_t)(e + p) * nl + (size_t)(l - l0)) * mm;
+        memset(B, 0, mm * sizeof(double));
+      }
+    }
+    double* C = out + ((size_t)p * nl + (size_t)(l - l0)) * mm;
+    for (int i = 0; i < m; ++i) {
+      double acc = 0.0;
+      for (int e = -p; e <= q; ++e) {
+        const double* B = out + ((size_t)(e + p) * nl + (size_t)(l - l0)) * mm;
+        for (int j = 0; j < m; ++j)
+          if (!(e == 0 && j == i)) acc += B[(size_t)i * m + j];
+      }
+      C[(size_t)i * m + i] = -acc;
+    }
+  }
+  return 0;
+}

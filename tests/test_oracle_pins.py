@@ -324,3 +324,70 @@ def test_observed_contraction_equals_bgs_and_eigenvalue():
     # block Jacobi does not converge (|lambda| = 1 twice)
     rj = ch.solve(tol=0.0, eps=1e-14, maxit=400, method=oracle.BJ)
     assert rj["sweeps"] == 400 and rj["step"] > 1e-6
+
+
+# --- block-banded Q^T: Algorithm 2 with off-staircase terms |k - i| >= 2 --------------
+
+def banded_dense_QT(D, L, m):
+    Q = np.zeros((L * m, L * m))
+    for e, B in D.items():
+        for l in range(L):
+            k = l + e
+            if 0 <= k < L:
+                Q[l * m:(l + 1) * m, k * m:(k + 1) * m] = B[l]
+    return Q.T.copy()
+
+
+@pytest.mark.parametrize("L,m,p,q", [(9, 3, 1, 3), (10, 2, 2, 2), (8, 4, 3, 1), (7, 1, 2, 3)])
+def test_banded_sweeps_equal_dense_splittings(L, m, p, q):
+    D = synth.banded(L, m, p, q, 0.8, seed=L + 10 * p + q)
+    bc = oracle.BandedChain(D)
+    T = banded_dense_QT(D, L, m)
+    assert np.array_equal(bc.dense_T(), T)
+    x = np.random.default_rng(L).random(L * m)
+    for meth, M in [(oracle.STAIR1, stair_M(T, L, m, 1)), (oracle.STAIR2, stair_M(T, L, m, 2)),
+                    (oracle.BGS, bgs_M(T, L, m)), (oracle.BJ, bj_M(T, L, m))]:
+        ref = np.linalg.solve(M, (M - T) @ x)
+        z = bc.sweep(x, meth)
+        assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), meth
+    assert abs(bc.residual(x) - np.abs(T @ x).sum()) <= 1e-13 * np.abs(T @ x).sum()
+
+
+def test_banded_reduces_to_tridiagonal_oracle():
+    dn, loc, up = synth.qbd(12, 4, 0.8, seed=2, level_dependent=True)
+    bc = oracle.BandedChain({-1: dn, 0: loc, 1: up})
+    ch = oracle.Chain(dn, loc, up)
+    x = np.random.default_rng(3).random(48)
+    for meth in (oracle.STAIR1, oracle.STAIR2, oracle.BGS, oracle.BJ):
+        assert np.allclose(bc.sweep(x, meth), ch.sweep(x, meth), rtol=1e-14, atol=0)
+
+
+def test_banded_limit_matches_direct_solve():
+    L, m = 14, 3
+    D = synth.banded(L, m, 1, 3, 0.7, seed=4)
+    bc = oracle.BandedChain(D)
+    res = bc.solve(tol=1e-14, maxit=200000, check_every=20)
+    T = banded_dense_QT(D, L, m)
+    T[-1, :] = 1.0
+    b = np.zeros(L * m); b[-1] = 1.0
+    ref = np.linalg.solve(T, b)
+    assert np.abs(res["x"] - ref).sum() <= 1e-11 and res["resid"] <= 1e-14
+
+
+def test_block_hessenberg_stair_rate_close_to_gauss_seidel():
+    """Sect. 2 / Example 3: on block Hessenberg singular M-matrices the staircase
+    spectral gap stays close to block Gauss-Seidel's (rho_2 near 1)."""
+    D = synth.banded(10, 3, 1, 3, 0.8, seed=7)
+    bc = oracle.BandedChain(D)
+
+    def gamma(meth):
+        G = np.empty((bc.N, bc.N))
+        for k in range(bc.N):
+            e = np.zeros(bc.N); e[k] = 1.0
+            G[:, k] = bc.sweep(e, meth)
+        ev = np.sort(np.abs(np.linalg.eigvals(G)))
+        assert abs(ev[-1] - 1.0) < 1e-9
+        return ev[-2]
+    g_bs, g_bgs = gamma(oracle.STAIR1), gamma(oracle.BGS)
+    rho2 = np.log(1 / g_bgs) / np.log(1 / g_bs)
+    assert 0.5 < rho2 < 2.0

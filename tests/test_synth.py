@@ -110,3 +110,29 @@ def test_request_stream():
     # log-uniform: median near sqrt(128*16384) = 1448
     assert 700 < np.median(Ls) < 3000
     assert reqs == synth.request_stream(200)
+
+
+@pytest.mark.parametrize("p,q", [(1, 3), (2, 2), (3, 1)])
+def test_banded_is_a_generator(p, q):
+    L, m = 23, 5
+    D = synth.banded(L, m, p, q, 0.8, seed=9)
+    Q = np.zeros((L * m, L * m))
+    for e, B in D.items():
+        for l in range(L):
+            k = l + e
+            if 0 <= k < L:
+                Q[l * m:(l + 1) * m, k * m:(k + 1) * m] = B[l]
+            else:
+                assert not B[l].any()
+    off = Q - np.diag(np.diag(Q))
+    assert (off >= 0).all()
+    assert np.abs(Q.sum(1)).max() <= 1e-13 * np.abs(Q).max() * m
+    n, _ = connected_components(sp.csr_matrix(off > 0), directed=True, connection="strong")
+    assert n == 1
+    l = L // 2
+    up = sum(D[e][l].sum() for e in range(1, q + 1))
+    dn = sum(D[e][l].sum() for e in range(-p, 0))
+    assert abs(up / dn - 0.8) < 1e-13
+    sub = synth.banded(L, m, p, q, 0.8, seed=9, l0=4, l1=11)
+    for e in D:
+        assert np.array_equal(sub[e], D[e][4:11])
