@@ -206,14 +206,22 @@ def run_mine(args):
     # inputs: synthetic generator blocks built on the host, copied once to HBM
     t0 = time.perf_counter()
     blocks = synth.workload(name)
-    d = [torch.from_numpy(b).to(dev) for b in blocks]
+    banded = isinstance(blocks, dict)
+    n_diags = len(blocks) if banded else 3
+    if banded:
+        d = {e: torch.from_numpy(b).to(dev) for e, b in blocks.items()}
+    else:
+        d = [torch.from_numpy(b).to(dev) for b in blocks]
     del blocks
     torch.cuda.synchronize()
     stream = torch.cuda.Stream(dev)
     # paired pentadiagonal workloads: skip the structurally zero quadrants
     paired = synth.WORKLOADS[name]["kind"] == "penta" and args.apply == "inverse" and m % 64 == 0
     with torch.cuda.stream(stream):
-        ch = mcl.Chain(*d, apply=args.apply, stream=stream, dtype=args.dtype, paired=paired)
+        if banded:
+            ch = mcl.Chain.banded(d, apply=args.apply, stream=stream, dtype=args.dtype)
+        else:
+            ch = mcl.Chain(*d, apply=args.apply, stream=stream, dtype=args.dtype, paired=paired)
     del d
     torch.cuda.synchronize()
     setup_s = time.perf_counter() - t0
@@ -277,6 +285,8 @@ def run_mine(args):
     # vector read once and z written once (16 m bytes); per sweep add reading
     # x and writing pi (16 N bytes) as counted for the whole step.
     nmat = 3 if args.apply == "inverse" else 2
+    if banded:
+        nmat = n_diags       # every off-diagonal block of Q^T plus (-T_dd)^{-1}
     if args.dtype == "f64":
         # paired chains stream 3/4 of each off-diagonal block
         mats = (2.5 if paired else nmat)
@@ -482,6 +492,40 @@ def run_serve(args):
     print(json.dumps(out), flush=True)
 
 
+def run_contraction(args):
+    """Observed contraction factor (step_k / step_{k-w})^(1/w) of the stair
+    splittings, block Jacobi and block Gauss-Seidel on one workload, from the
+    uniform start, with the GPU sweeps/s of each (Sect. 2: on block-tridiagonal
+    Q^T the staircase and block Gauss-Seidel share their spectrum)."""
+    import torch
+
+    import synth
+    import paper_2302_07551_gb300 as mcl
+
+    torch.cuda.set_device(0)
+    name = args.workload
+    L, m = synth.workload_shape(name)
+    blocks = synth.workload(name)
+    d = [torch.from_numpy(b).cuda() for b in blocks]
+    del blocks
+    torch.cuda.synchronize()
+    rows = {}
+    for stair, label, nsw in ((1, "stair1", args.steps), (2, "stair2", args.steps),
+                              (3, "block_jacobi", args.steps), (4, "block_gauss_seidel",
+                                                                args.bgs_steps)):
+        ch = mcl.Chain(*d, stair=stair)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, res = ch.solve(tol=0.0, eps=0.0, maxit=nsw, check_every=min(args.refine_every, nsw))
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        rows[label] = {"sweeps": nsw, "contraction": res["contraction"], "step": res["step"],
+                       "residual": res["residual"], "sweeps_s": nsw / t}
+        ch.close()
+    print(json.dumps({"mode": "contraction", "workload": name, "L": L, "m": m,
+                      "window": args.refine_every, "results": rows}), flush=True)
+
+
 def measure_fp64_peak():
     """FP64 multiply-add peak of this GPU: cuBLAS DGEMM 8192^3, best of 10,
     with the SM clock sampled meanwhile."""
@@ -521,6 +565,9 @@ def main():
                     help="time one full solve to --tol per dtype instead of sweeps")
     ap.add_argument("--tol", type=float, default=1e-12)
     ap.add_argument("--serve", action="store_true", help="serving benchmark on the request stream")
+    ap.add_argument("--contraction", action="store_true",
+                    help="contraction factors of stair / block Jacobi / block Gauss-Seidel")
+    ap.add_argument("--bgs-steps", type=int, default=200)
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--serve-dtype", default="bf16", choices=["f64", "f32", "bf16"])
     ap.add_argument("--serve-tol", type=float, default=1e-10)
@@ -542,6 +589,8 @@ def main():
         run_solve(args)
     elif args.serve:
         run_serve(args)
+    elif args.contraction:
+        run_contraction(args)
     else:
         run_mine(args)
 

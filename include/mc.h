@@ -106,6 +106,13 @@ typedef struct {
                       rows ..m/2 x columns m/2..; the FP64 sweep and residual skip
                       those quadrants.  Needs m % 64 == 0; mc_factor checks that the
                       quadrants are zero (MC_ERR_ARG otherwise).                 */
+  int32_t lower;   /* block bandwidths of the generator: Q_{l,l+e} may be nonzero */
+  int32_t upper;   /* only for -lower <= e <= upper (0 means 1, block tridiagonal).
+                      Wider bands (block Hessenberg / banded, up to 5 each side)
+                      need mc_create_banded, apply = MC_APPLY_INVERSE, MC_F64 and
+                      paired = 0; the sweeps then carry Algorithm 2's
+                      off-staircase terms |k - i| >= 2, read from the sweep's
+                      input vector.                                                 */
 } mc_desc;
 
 typedef struct {
@@ -137,6 +144,17 @@ size_t mc_workspace_bytes(const mc_desc* desc);
  */
 int mc_create(const mc_desc* desc, const double* dn, const double* loc, const double* up,
               void* workspace, size_t ws_bytes, void* cuda_stream, mc_chain** out);
+
+/*
+ * As mc_create for a block-banded generator (desc->lower, desc->upper):
+ * diags[e + lower], e = -lower..upper, are device pointers to L blocks of
+ * m x m doubles, row-major, diags[e + lower][l] = Q_{l,l+e} (e = 0: the
+ * diagonal blocks with their diagonal).  Blocks whose level l+e lies outside
+ * [0, L) are ignored.  The Q^T block (l, l+d) is (Q_{l+d,l})^T (Sect. 2).
+ * Async.  Errors as mc_create.
+ */
+int mc_create_banded(const mc_desc* desc, const double* const* diags, void* workspace,
+                     size_t ws_bytes, void* cuda_stream, mc_chain** out);
 
 /*
  * Factor the diagonal blocks Q_{i,i} (as blocks of Q^T) by batched LU without

@@ -18,7 +18,8 @@ PLANES = {"tlo": 0, "tup": 1, "tdd": 2, "lu": 3, "ninv": 4, "wlo": 5, "wup": 6}
 
 class McDesc(ctypes.Structure):
     _fields_ = [("L", ctypes.c_int64), ("m", ctypes.c_int32), ("stair", ctypes.c_int32),
-                ("apply", ctypes.c_int32), ("dtype", ctypes.c_int32), ("paired", ctypes.c_int32)]
+                ("apply", ctypes.c_int32), ("dtype", ctypes.c_int32), ("paired", ctypes.c_int32),
+                ("lower", ctypes.c_int32), ("upper", ctypes.c_int32)]
 
 
 class McServerDesc(ctypes.Structure):
@@ -52,6 +53,8 @@ def load():
     lib.mc_workspace_bytes.restype = sz
     lib.mc_create.argtypes = [pdesc, vp, vp, vp, vp, sz, vp, ctypes.POINTER(vp)]
     lib.mc_create.restype = ctypes.c_int
+    lib.mc_create_banded.argtypes = [pdesc, ctypes.POINTER(vp), vp, sz, vp, ctypes.POINTER(vp)]
+    lib.mc_create_banded.restype = ctypes.c_int
     lib.mc_factor.argtypes = [vp]
     lib.mc_factor.restype = ctypes.c_int
     lib.mc_sweep.argtypes = [vp, vp, vp, i64, vp]

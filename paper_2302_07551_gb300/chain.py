@@ -30,16 +30,24 @@ class Chain:
     """
 
     def __init__(self, dn, loc, up, stair=1, apply="inverse", stream=None, factor=True,
-                 dtype="f64", paired=False):
+                 dtype="f64", paired=False, diags=None):
         lib = nat.load()
-        for t, n in ((dn, "dn"), (loc, "loc"), (up, "up")):
-            _need(t, loc.shape, n)
+        if diags is not None:
+            # block-banded: diags = {e: (L, m, m) tensor of Q[l, l+e]}
+            lower, upper = -min(diags), max(diags)
+            loc = diags[0]
+            for e, t in diags.items():
+                _need(t, loc.shape, f"diags[{e}]")
+        else:
+            lower = upper = 1
+            for t, n in ((dn, "dn"), (loc, "loc"), (up, "up")):
+                _need(t, loc.shape, n)
         L, m, _ = loc.shape
         self.L, self.m, self.N = int(L), int(m), int(L) * int(m)
         self.device = loc.device
         self.desc = nat.McDesc(self.L, self.m, int(stair),
                                nat.MC_APPLY_COUPLED if apply == "coupled" else nat.MC_APPLY_INVERSE,
-                               nat.DTYPES[dtype], 1 if paired else 0)
+                               nat.DTYPES[dtype], 1 if paired else 0, lower, upper)
         self.dtype = dtype
         self.apply = apply
         nbytes = lib.mc_workspace_bytes(ctypes.byref(self.desc))
@@ -51,10 +59,18 @@ class Chain:
         self._ws_ptr = (base + 255) // 256 * 256
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         h = ctypes.c_void_p()
-        nat.check(lib.mc_create(ctypes.byref(self.desc), _ptr(dn), _ptr(loc), _ptr(up),
-                                ctypes.c_void_p(self._ws_ptr), nbytes,
-                                ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
-                  "mc_create")
+        if diags is not None:
+            arr = (ctypes.c_void_p * (lower + upper + 1))(
+                *[diags[e].data_ptr() for e in range(-lower, upper + 1)])
+            nat.check(lib.mc_create_banded(ctypes.byref(self.desc), arr,
+                                           ctypes.c_void_p(self._ws_ptr), nbytes,
+                                           ctypes.c_void_p(self.stream.cuda_stream),
+                                           ctypes.byref(h)), "mc_create_banded")
+        else:
+            nat.check(lib.mc_create(ctypes.byref(self.desc), _ptr(dn), _ptr(loc), _ptr(up),
+                                    ctypes.c_void_p(self._ws_ptr), nbytes,
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h)),
+                      "mc_create")
         self._h = h
         self._lib = lib
         if factor:
@@ -145,6 +161,11 @@ class Chain:
             self.close()
         except Exception:
             pass
+
+    @classmethod
+    def banded(cls, diags, **kw):
+        """Block-banded chain from {e: (L, m, m) float64 CUDA tensor of Q[l, l+e]}."""
+        return cls(None, None, None, diags=diags, **kw)
 
 
 def solve(dn, loc, up, tol=1e-12, **kw):

@@ -18,7 +18,10 @@ static bool desc_ok(const mc_desc* d) {
          (d->stair <= 2 || (d->dtype == MC_F64 && d->paired == 0)) &&
          (d->apply == MC_APPLY_INVERSE || d->apply == MC_APPLY_COUPLED) &&
          (d->dtype == MC_F64 || ((d->dtype == MC_F32 || d->dtype == MC_BF16) && d->m % 4 == 0)) &&
-         (d->paired == 0 || (d->paired == 1 && d->m % 64 == 0));
+         (d->paired == 0 || (d->paired == 1 && d->m % 64 == 0)) &&
+         d->lower >= 0 && d->lower <= 5 && d->upper >= 0 && d->upper <= 5 &&
+         ((d->lower <= 1 && d->upper <= 1) ||
+          (d->apply == MC_APPLY_INVERSE && d->dtype == MC_F64 && d->paired == 0));
 }
 
 Layout make_layout(const mc_desc& d) {
@@ -28,6 +31,14 @@ Layout make_layout(const mc_desc& d) {
   y.N = d.L * d.m;
   y.ms = (int)round_up((size_t)d.m * d.m, 32);
   y.n_planes = d.apply == MC_APPLY_COUPLED ? 7 : 5;
+  // off-staircase diagonals of Q^T: offsets -upper..-2 and 2..lower (the
+  // Q^T block (l, l+d) is (Q_{l+d,l})^T, so Q's upper band is Q^T's lower)
+  const int lo = d.lower > 1 ? d.lower : 1, up = d.upper > 1 ? d.upper : 1;
+  y.nfar = 0;
+  y.far_base = y.n_planes;
+  for (int o = -up; o <= -2; ++o) y.far_off[y.nfar++] = o;
+  for (int o = 2; o <= lo; ++o) y.far_off[y.nfar++] = o;
+  y.n_planes += y.nfar;
   y.plane_bytes = (size_t)d.L * y.ms * sizeof(double);
   y.vec_bytes = round_up((size_t)y.N, 32) * sizeof(double);
   size_t o = 0;
@@ -105,6 +116,8 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.ms = c->lay.ms;
   a.stride = 2;
   a.s_prev = scaled_src ? &c->hdr->stats[0] : nullptr;
+  a.far = c->lay.nfar ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
+  a.xfar = src;
   if (c->d.stair >= 3) {
     // comparison splittings of Sect. 2: block Jacobi (every level from x, one
     // launch) and block Gauss-Seidel (levels in order, one warp)
@@ -177,7 +190,9 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
 // passes instead of n.
 static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
                           double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr) {
-  const bool lagged = c->d.stair <= 2 && n > 2;
+  // (block-banded chains read x for the far terms of both half-sweeps, so
+  // the previous iterate must be stored)
+  const bool lagged = c->d.stair <= 2 && n > 2 && c->lay.nfar == 0;
   for (int64_t k = 0; k < n; ++k) {
     cudaEvent_t* e = ev ? ev + 4 * k : nullptr;
     int rc;
@@ -211,6 +226,7 @@ static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float*
   r.m = c->lay.m;
   r.ms = c->lay.ms;
   r.paired = c->d.paired;
+  r.far = c->lay.nfar ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
   CK(launch_residual(r, c->nb_resid, s));
   return MC_OK;
 }
@@ -360,6 +376,7 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   if (!out) return MC_ERR_ARG;
   *out = nullptr;
   if (!desc_ok(desc) || !dn || !loc || !up) return MC_ERR_ARG;
+  if (desc->lower > 1 || desc->upper > 1) return MC_ERR_ARG;
   if (((uintptr_t)dn | (uintptr_t)loc | (uintptr_t)up) & 7u) return MC_ERR_ARG;
   mc_chain* c = nullptr;
   const int rc = chain_init(desc, workspace, ws_bytes, (cudaStream_t)cuda_stream, &c);
@@ -367,6 +384,45 @@ int mc_create(const mc_desc* desc, const double* dn, const double* loc, const do
   if (launch_layout(dn, loc, up, c->planes, c->lay, c->hdr, c->user) != cudaSuccess) {
     mc_destroy(c);
     return MC_ERR_CUDA;
+  }
+  *out = c;
+  return MC_OK;
+}
+
+int mc_create_banded(const mc_desc* desc, const double* const* diags, void* workspace,
+                     size_t ws_bytes, void* cuda_stream, mc_chain** out) {
+  if (!out) return MC_ERR_ARG;
+  *out = nullptr;
+  if (!desc_ok(desc) || !diags) return MC_ERR_ARG;
+  const int lo = desc->lower > 1 ? desc->lower : 1, up = desc->upper > 1 ? desc->upper : 1;
+  for (int e = -lo; e <= up; ++e)
+    if (!diags[e + lo] || ((uintptr_t)diags[e + lo] & 7u)) return MC_ERR_ARG;
+  mc_chain* c = nullptr;
+  int rc = chain_init(desc, workspace, ws_bytes, (cudaStream_t)cuda_stream, &c);
+  if (rc != MC_OK) return rc;
+  const Layout& y = c->lay;
+  const size_t pe = y.plane_bytes / sizeof(double);
+  // near diagonals as in mc_create: Q^T (l, l-1) <- Q_{l-1,l} (e = +1),
+  // (l, l+1) <- Q_{l+1,l} (e = -1), (l, l) <- Q_{l,l}
+  if (launch_layout(diags[lo - 1], diags[lo], diags[lo + 1], c->planes, y, c->hdr, c->user) !=
+      cudaSuccess)
+    rc = MC_ERR_CUDA;
+  FarDesc fd{};
+  fd.n = y.nfar;
+  for (int j = 0; j < y.nfar && rc == MC_OK; ++j) {
+    const int d = y.far_off[j];
+    double* plane = c->planes + (size_t)(y.far_base + j) * pe;
+    fd.off[j] = d;
+    fd.plane[j] = plane;
+    if (launch_layout_diag(diags[-d + lo], d, plane, y, c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+  }
+  if (rc == MC_OK && cudaMemcpyAsync((char*)c->hdr + kFarDescOffset, &fd, sizeof(fd),
+                                     cudaMemcpyHostToDevice, c->user) != cudaSuccess)
+    rc = MC_ERR_CUDA;
+  if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+  if (rc != MC_OK) {
+    mc_destroy(c);
+    return rc;
   }
   *out = c;
   return MC_OK;
@@ -464,7 +520,7 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   ms_host[2] = t[2];
   // kernel launches: 2 per sweep (1 for the comparison splittings) plus the
   // normalisations (1 per sweep unless the lagged scheme keeps them to 2)
-  const bool lagged = !c->lay.lp && c->d.stair <= 2 && nsweeps > 2;
+  const bool lagged = !c->lay.lp && c->d.stair <= 2 && nsweeps > 2 && c->lay.nfar == 0;
   const double per = c->lay.lp ? 2.0 : (c->d.stair <= 2 ? 2.0 : 1.0);
   ms_host[3] = per * (double)nsweeps + (c->lay.lp ? 1.0 : (lagged ? 2.0 : (double)nsweeps));
   return sync_header(c);

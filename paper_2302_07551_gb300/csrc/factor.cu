@@ -290,7 +290,27 @@ __global__ void k_check_paired(const double* __restrict__ tlo, const double* __r
   if (bad) latch(hdr, MC_ERR_ARG);
 }
 
+__global__ void k_layout_diag(const double* __restrict__ diag, int d, double* __restrict__ plane,
+                              int64_t L, int m, int ms) {
+  const int64_t mm = (int64_t)m * m;
+  const int64_t total = L * ms;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t l = t / ms, e = t % ms, k = l + d;
+    plane[t] = (e < mm && k >= 0 && k < L) ? diag[k * mm + e] : 0.0;
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_layout_diag(const double* diag, int d, double* plane, const Layout& lay,
+                               cudaStream_t s) {
+  const int64_t total = lay.L * lay.ms;
+  int nb = (int)((total + 255) / 256);
+  if (nb > 4096) nb = 4096;
+  k_layout_diag<<<nb, 256, 0, s>>>(diag, d, plane, lay.L, lay.m, lay.ms);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_check_paired(const double* tlo, const double* tup, const Layout& lay,
                                 Header* hdr, cudaStream_t s) {

@@ -31,6 +31,16 @@ struct Header {
   double stats[4];       // [e^T z, step_l1, resid_l1, spare]
 };
 
+// Off-staircase block diagonals |d| >= 2 of a block-banded Q^T (device
+// resident in the workspace header region).
+constexpr int kMaxFar = 8;
+struct FarDesc {
+  int32_t n;
+  int32_t off[kMaxFar];           // d: the Q^T block (l, l + d)
+  const double* plane[kMaxFar];   // L blocks, column-major, stride ms
+};
+constexpr size_t kFarDescOffset = 512;   // byte offset inside the 4 KB header
+
 // Plane indices match mc_plane.
 constexpr int kPlaneTLO = 0, kPlaneTUP = 1, kPlaneTDD = 2, kPlaneLU = 3, kPlaneNINV = 4,
               kPlaneWLO = 5, kPlaneWUP = 6;
@@ -39,6 +49,9 @@ struct Layout {
   int64_t L, N;
   int m, ms;             // block size and padded block stride (doubles)
   int n_planes;
+  int nfar;              // off-staircase diagonals (block-banded chains)
+  int far_off[kMaxFar];
+  int far_base;          // plane index of the first far diagonal
   size_t plane_bytes, vec_bytes;
   size_t off_hdr, off_planes, off_z, off_xa, off_xb, off_wpart, off_dpart, off_rpart, total;
   // low-precision storage (dtype MC_F32 / MC_BF16)
@@ -58,6 +71,8 @@ struct PhaseArgs {
   const double* src;     // vector read at neighbour levels l-1, l+1
   const double* src_up;  // if set: vector read at level l+1 instead (block Gauss-Seidel)
   const double* s_prev;  // if set: src is an unnormalised z, scaled by 1 / *s_prev on read
+  const FarDesc* far;    // if set: off-staircase diagonals, read from xfar
+  const double* xfar;    // the sweep's input x (far terms of both half-sweeps)
   double* dst;           // z, written at this half-sweep's levels
   double* wpart;         // one level-sum partial per warp
   Header* hdr;
@@ -94,11 +109,16 @@ struct ResidArgs {
   int64_t L;
   int m, ms;
   int paired;
+  const FarDesc* far;
 };
 
 // Launchers (return cudaGetLastError()).
 cudaError_t launch_layout(const double* dn, const double* loc, const double* up, double* planes,
                           const Layout& lay, Header* hdr, cudaStream_t s);
+// Q^T diagonal d into a plane: plane[l] = diag[l + d] (row-major Q block =
+// column-major Q^T block), zero where l + d is outside [0, L).
+cudaError_t launch_layout_diag(const double* diag, int d, double* plane, const Layout& lay,
+                               cudaStream_t s);
 cudaError_t launch_factor(double* planes, const Layout& lay, Header* hdr, int coupled,
                           int num_sms, cudaStream_t s);
 cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStream_t s);

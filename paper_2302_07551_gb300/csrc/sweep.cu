@@ -47,8 +47,8 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   const double scale = a.s_prev ? 1.0 / *a.s_prev : 1.0;
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = a.stride * u + a.parity;
-    wsum += level_sweep<R, COUPLED, PAIRED>(a.A, a.B, a.C, a.src, a.dst, l, a.L, a.m, a.ms, slice,
-                                            lane, scale);
+    wsum += level_sweep2<R, COUPLED, PAIRED>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L, a.m,
+                                             a.ms, slice, lane, scale, a.far, a.xfar, a.xfar);
   }
   if (lane == 0) {
     a.wpart[gw] = wsum;
@@ -83,7 +83,7 @@ __global__ void __launch_bounds__(32) k_bgs(PhaseArgs a) {
   double s = 0.0;
   for (int64_t l = 0; l < a.L; ++l) {
     s += level_sweep2<R, COUPLED>(a.A, a.B, a.C, a.dst, a.src_up, a.dst, l, a.L, a.m, a.ms, slice,
-                                  lane);
+                                  lane, 1.0, a.far, a.dst, a.src_up);
     __syncwarp();   // z_l (global, written by all lanes) is read by all lanes next
   }
   if (lane == 0) a.hdr->stats[0] = s;
@@ -169,7 +169,7 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   double wsum = 0.0;
   for (int64_t l = gw; l < a.L; l += nw)
     wsum += level_resid<R, PAIRED>(a.TLO, a.TDD, a.TUP, a.NINV, a.x, WITH_Q ? a.q : nullptr, l,
-                                   a.L, a.m, a.ms, slice, lane);
+                                   a.L, a.m, a.ms, slice, lane, a.far);
   if (lane == 0) {
     a.rpart[gw] = wsum;
     __threadfence();

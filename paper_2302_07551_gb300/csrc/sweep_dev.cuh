@@ -155,11 +155,32 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // z_l = W_lo v_{l-1} + W_up v_{l+1} (coupled: A = W_lo, B = W_up), written to
 // dst; returns sum_i z_l[i] on every lane.  slice: 3 * 32 R doubles of the
 // warp's shared memory.
+// Off-staircase terms of a block-banded Q^T: acc += sum_j T_{l,l+d_j} v_{l+d_j}
+// with v = xlo for d_j < 0 and xup for d_j > 0 (staged through slice).
+template <int R>
+__device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const FarDesc* far,
+                                          const double* xlo, const double* xup, int64_t l,
+                                          int64_t L, int m, int ms, double* slice, int lane) {
+  const int n = far->n;
+  for (int j = 0; j < n; ++j) {
+    const int64_t k = l + far->off[j];
+    if (k < 0 || k >= L) continue;
+    __syncwarp();
+    stage_vec<R>(slice, (far->off[j] < 0 ? xlo : xup) + k * m, m, lane);
+    __syncwarp();
+    gemv_acc<R>(acc, far->plane[j] + (size_t)l * ms, slice, m, lane);
+  }
+  __syncwarp();
+}
+
 template <int R, bool COUPLED, bool PAIRED = false>
 __device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
                                                const double* src, const double* src_up,
                                                double* dst, int64_t l, int64_t L, int m, int ms,
-                                               double* slice, int lane, double scale = 1.0) {
+                                               double* slice, int lane, double scale = 1.0,
+                                               const FarDesc* far = nullptr,
+                                               const double* xfar_lo = nullptr,
+                                               const double* xfar_up = nullptr) {
   constexpr int NA = Tune<R>::NA, W = 32 * R;
   double* v_lo = slice;
   double* v_up = slice + W;
@@ -177,6 +198,7 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
     if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
     if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
   }
+  if (far) far_terms<R>(acc, far, xfar_lo, xfar_up, l, L, m, ms, v_lo, lane);
   if (!COUPLED) {
 #pragma unroll
     for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
@@ -215,7 +237,8 @@ template <int R, bool PAIRED = false>
 __device__ __forceinline__ double level_resid(const double* TLO, const double* TDD,
                                               const double* TUP, const double* NINV,
                                               const double* x, float* q, int64_t l, int64_t L,
-                                              int m, int ms, double* slice, int lane) {
+                                              int m, int ms, double* slice, int lane,
+                                              const FarDesc* far = nullptr) {
   constexpr int NA = Tune<R>::NA, W = 32 * R;
   double* v_lo = slice;
   double* v_dd = slice + W;
@@ -239,6 +262,7 @@ __device__ __forceinline__ double level_resid(const double* TLO, const double* T
     else
       gemv_acc<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
   }
+  if (far) far_terms<R>(acc, far, x, x, l, L, m, ms, v_lo, lane);
   double ls = 0.0;
 #pragma unroll
   for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));

@@ -30,6 +30,8 @@ WORKLOADS = {
     "birth_death_L64": dict(kind="birth_death", L=64, m=1, lam=0.8, mu=1.0),
     # L=32768, m=64, level-dependent, ratio 0.9 (FP64 blocks ~3.2 GB)
     "qbd_L32768_m64": dict(kind="qbd", L=32768, m=64, ratio=0.9, level_dependent=True, seed=1),
+    # same recipe at L=512: contraction comparisons that run to the asymptotic regime
+    "qbd_L512_m64": dict(kind="qbd", L=512, m=64, ratio=0.9, level_dependent=True, seed=1),
     # same recipe at L=8192 (0.8 GB of blocks per sweep): profiling-size case
     "qbd_L8192_m64": dict(kind="qbd", L=8192, m=64, ratio=0.9, level_dependent=True, seed=1),
     # block Hessenberg: batch arrivals of up to 4 levels, single-level service;

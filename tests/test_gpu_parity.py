@@ -316,3 +316,33 @@ def test_multi_sweep_call_equals_single_sweeps_bitwise():
         assert torch.equal(a, b)
         assert torch.equal(st_a[:2], st_b[:2])
     ch.close()
+
+
+# --- block-banded chains: Algorithm 2 with off-staircase terms ------------------------
+
+@pytest.mark.parametrize("L,m,p,q", [(40, 16, 1, 4), (33, 64, 3, 1), (21, 40, 2, 3), (12, 160, 1, 2)])
+def test_banded_sweeps_residual_and_solve(L, m, p, q):
+    D = synth.banded(L, m, p, q, 0.8, seed=L + m + p)
+    bc = oracle.BandedChain(D)
+    dd = {e: dev(B) for e, B in D.items()}
+    N = L * m
+    for stair, meth in ((1, oracle.STAIR1), (2, oracle.STAIR2), (3, oracle.BJ), (4, oracle.BGS)):
+        ch = mc.Chain.banded(dd, stair=stair)
+        x = ch.sweep(torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda"), nsweeps=15)
+        ref = bc.sweeps(np.full(N, 1.0 / N), 15, method=meth)
+        assert rel_l1(x.cpu().numpy(), ref) <= 1e-12, stair
+        ch.close()
+    ch = mc.Chain.banded(dd)
+    y = np.random.default_rng(2).random(N)
+    assert abs(ch.residual(dev(y)) - bc.residual(y)) <= 1e-12 * bc.residual(y)
+    pi, res = ch.solve(tol=1e-12, maxit=200000, check_every=32)
+    sol = bc.solve(tol=1e-13, maxit=200000, check_every=50)["x"]
+    assert res["converged"] and rel_l1(pi.cpu().numpy(), sol) <= 1e-10
+    ch.close()
+
+
+def test_banded_restrictions():
+    D = {e: dev(B) for e, B in synth.banded(8, 8, 1, 3, 0.8, seed=1).items()}
+    for kw in (dict(apply="coupled"), dict(dtype="f32")):
+        with pytest.raises(ValueError):
+            mc.Chain.banded(D, **kw)
