@@ -47,9 +47,11 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   const double scale = a.s_prev ? 1.0 / *a.s_prev : 1.0;
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = a.stride * u + a.parity;
-    wsum += level_sweep2<R, COUPLED, PAIRED>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L, a.m,
-                                             a.ms, slice, lane, scale, a.far, a.xfar, a.xfar);
+    wsum += level_sweep2<R, COUPLED, PAIRED, false>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L,
+                                                    a.m, a.ms, slice, lane, scale, a.far, a.xfar,
+                                                    a.xfar);
   }
+  wsum = warp_sum(wsum);   // the lanes' partials over all of this warp's levels
   if (lane == 0) {
     a.wpart[gw] = wsum;
     if (a.reduce_s) __threadfence();

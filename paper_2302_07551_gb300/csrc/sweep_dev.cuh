@@ -24,7 +24,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int R>
 struct Tune {
   static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
-  static constexpr int NA = R <= 2 ? 4 : 2;                            // accumulators per row
+  static constexpr int NA = 2;                                         // accumulators per row
   static constexpr int MINB = R <= 4 ? 3 : 2;                          // blocks per SM
 };
 
@@ -114,10 +114,18 @@ __device__ __forceinline__ void gemv_up_paired(double (&acc)[R][Tune<R>::NA],
 template <int R>
 __device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
                                           int lane, double scale = 1.0) {
+  if (scale != 1.0) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int row = lane + 32 * r;
-    v[row] = row < m ? p[row] * scale : 0.0;
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      v[row] = row < m ? p[row] * scale : 0.0;
+    }
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      v[row] = row < m ? p[row] : 0.0;
+    }
   }
 }
 
@@ -173,7 +181,9 @@ __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const F
   __syncwarp();
 }
 
-template <int R, bool COUPLED, bool PAIRED = false>
+// Returns sum_i z_l[i]: on every lane (WARP_TOTAL) or the lane's own rows
+// only (callers that only need a total over many levels reduce once at the end).
+template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true>
 __device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
                                                const double* src, const double* src_up,
                                                double* dst, int64_t l, int64_t L, int m, int ms,
@@ -216,7 +226,7 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
       ls += zr;
     }
   }
-  const double total = warp_sum(ls);
+  const double total = WARP_TOTAL ? warp_sum(ls) : ls;
   __syncwarp();   // the slice is rewritten for the next level
   return total;
 }

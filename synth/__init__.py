@@ -40,6 +40,8 @@ WORKLOADS = {
                                  seed=5),
     # jumps +-1, +-2 on L=8192 levels of m=128, paired to 4096 levels of 256
     "penta_L8192_m128": dict(kind="penta", L=8192, m=128, ratio=0.8, scale2=0.3, seed=2),
+    # same recipe at L=2048 (1024 paired levels of 256; 1.3 GB per sweep): profiling size
+    "penta_L2048_m128": dict(kind="penta", L=2048, m=128, ratio=0.8, scale2=0.3, seed=2),
     # same recipe at L=1024 (time-to-solution comparisons)
     "qbd_L1024_m256": dict(kind="qbd", L=1024, m=256, ratio=0.9, level_dependent=True, seed=3),
     # L=16384, m=256, level-dependent, ratio 0.9 (FP64 blocks ~25.8 GB)
