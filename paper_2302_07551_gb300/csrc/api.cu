@@ -326,17 +326,18 @@ int mc::chain_init(const mc_desc* desc, void* workspace, size_t ws_bytes, cudaSt
   c->wpart = (double*)(c->ws + lay.off_wpart);
   c->dpart = (double*)(c->ws + lay.off_dpart);
   c->rpart = (double*)(c->ws + lay.off_rpart);
-  // persistent grids: as many resident warps as the kernel's occupancy gives,
-  // never more warps than levels
+  // persistent grids: the full resident grid of the kernel's occupancy (a
+  // multiple of the SM count) once there is at least one unit per SM, else one
+  // warp per unit
   const int64_t pmax = (lay.L + 1) / 2;
   const int64_t wps = (int64_t)kWarpsPerBlock * phase_blocks_per_sm(lay.m);
   int64_t w = wps * sms;
-  if (w > pmax) w = pmax;
+  if (pmax < sms) w = pmax;
   if (w > kMaxWarps) w = kMaxWarps;
   c->nb_phase = (int)((w + kWarpsPerBlock - 1) / kWarpsPerBlock);
   c->nw = c->nb_phase * kWarpsPerBlock;
   int64_t wr = wps * sms;
-  if (wr > lay.L) wr = lay.L;
+  if (lay.L < sms) wr = lay.L;
   if (wr > kMaxWarps) wr = kMaxWarps;
   c->nb_resid = (int)((wr + kWarpsPerBlock - 1) / kWarpsPerBlock);
   int64_t nbn = (lay.N + 4 * kNormThreads - 1) / (4 * kNormThreads);

@@ -19,6 +19,7 @@
 
 #include "mc_internal.cuh"
 #include "lowprec_dev.cuh"
+#include "sweep_dev.cuh"
 
 namespace mc {
 
@@ -45,8 +46,8 @@ __global__ void __launch_bounds__(256) k_phase_lp(LpArgs a) {
   constexpr int SL = LpSlice<T, G, GF>::SL;
   const int lane = threadIdx.x & 31;
   float* slice = fsh + (threadIdx.x >> 5) * 3 * SL;
-  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int gw = sched_warp(a.P, nw);
   const T* Ap = reinterpret_cast<const T*>(a.A);
   const T* Bp = reinterpret_cast<const T*>(a.B);
   for (int64_t u = gw; u < a.P; u += nw) {

@@ -41,8 +41,8 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   __shared__ bool last;
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
-  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int gw = sched_warp(a.P, nw);
   double wsum = 0.0;
   const double scale = a.s_prev ? 1.0 / *a.s_prev : 1.0;
   for (int64_t u = gw; u < a.P; u += nw) {
@@ -166,8 +166,8 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_residual(ResidArgs a) {
   __shared__ bool last;
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
-  const int gw = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
+  const int gw = sched_warp(a.L, nw);
   double wsum = 0.0;
   for (int64_t l = gw; l < a.L; l += nw)
     wsum += level_resid<R, PAIRED>(a.TLO, a.TDD, a.TUP, a.NINV, a.x, WITH_Q ? a.q : nullptr, l,

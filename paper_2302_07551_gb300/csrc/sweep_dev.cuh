@@ -21,6 +21,17 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Warp index for the persistent loop  for (u = w; u < P; u += nw).  With
+// several rounds it is block-major: a block's warps take consecutive units, so
+// the grid streams one window of neighbouring levels.  When all P units fit in
+// one partial round it is block-minor instead, so that the busy warps spread
+// evenly over the blocks (hence over the SMs) rather than filling the first
+// blocks.  Both orders are permutations of [0, nw).
+__device__ __forceinline__ int sched_warp(int64_t P, int nw) {
+  if (P >= nw) return (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  return (int)((threadIdx.x >> 5) * gridDim.x + blockIdx.x);
+}
+
 template <int R>
 struct Tune {
   static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
