@@ -184,6 +184,16 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def src_hash(sources):
+    """First 16 hex digits of the SHA-256 of the named csrc files, in order."""
+    import hashlib
+    hs = hashlib.sha256()
+    for src in sources:
+        with open(os.path.join(ROOT, "paper_2302_07551_gb300", "csrc", src), "rb") as f:
+            hs.update(f.read())
+    return hs.hexdigest()[:16]
+
+
 def run_mine(args):
     import numpy as np
     import torch
@@ -300,12 +310,29 @@ def run_mine(args):
         bytes_level = mat + 16 * m
         sweep_bytes = L * bytes_level
     flops_level = int(2 * (2.5 if (paired and args.dtype == "f64") else nmat) * m * m)
-    half_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * prof_steps)
-    half_bytes = bytes_level * L / 2
-    half_flops = flops_level * L / 2
+    # dominant kernel: the fused sweep kernel (one launch runs all timed
+    # sweeps, up to 1024 per launch) or, for the low-precision correction
+    # sweeps, one half-sweep launch
+    fused = prof.get("fused", False)
+    if fused:
+        sweeps_per_launch = min(prof_steps, 1024)
+        n_launch = -(-prof_steps // 1024)
+        kern_ms = prof["sweeps_ms"] / n_launch
+        kern_bytes = bytes_level * L * sweeps_per_launch
+        kern_flops = flops_level * L * sweeps_per_launch
+        kern_ms_per_sweep = {"sweeps": prof["sweeps_ms"] / prof_steps,
+                             "scale": prof["scale_ms"] / prof_steps,
+                             "normalise": prof["norm_ms"] / prof_steps}
+    else:
+        kern_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * prof_steps)
+        kern_bytes = bytes_level * L / 2
+        kern_flops = flops_level * L / 2
+        kern_ms_per_sweep = {"half1": prof["half1_ms"] / prof_steps,
+                             "half2": prof["half2_ms"] / prof_steps,
+                             "normalise": prof["norm_ms"] / prof_steps}
     hbm_peak, hbm_src = peaks()
-    achieved_gbs = half_bytes / (half_ms * 1e-3) / 1e9
-    achieved_tf = half_flops / (half_ms * 1e-3) / 1e12
+    achieved_gbs = kern_bytes / (kern_ms * 1e-3) / 1e9
+    achieved_tf = kern_flops / (kern_ms * 1e-3) / 1e12
     if rank != 0:
         if ws > 1:
             torch.distributed.destroy_process_group()
@@ -314,25 +341,23 @@ def run_mine(args):
     if ws == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+    kname = "k_sweeps" if fused else "k_phase"
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if os.path.exists(tp):
-        import hashlib
+    if args.dtype == "f64" and os.path.exists(tp):
         with open(tp) as f:
-            tj = json.load(f)
-        hs = hashlib.sha256()
-        for src in ("sweep.cu", "sweep_dev.cuh"):
-            with open(os.path.join(ROOT, "paper_2302_07551_gb300", "csrc", src), "rb") as f:
-                hs.update(f.read())
-        sha = hs.hexdigest()[:16]
+            tk = json.load(f).get("kernels", {}).get(kname)
         key = f"{name}:{args.apply}"
         # counters taken on an older kernel source do not describe this one
-        if args.dtype == "f64" and key in tj and tj.get("kernel_src_sha256") == sha:
-            traffic = tj[key]["bytes_per_launch"]
+        if tk and key in tk["workloads"] and tk["kernel_src_sha256"] == src_hash(tk["sources"]):
+            w = tk["workloads"][key]
+            traffic = w["bytes_per_sweep"] * sweeps_per_launch if fused else w["bytes_per_launch"]
     if args.dtype == "f64":
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
-                "traffic": traffic, "kernel": "k_phase (one half-sweep)",
+                "traffic": traffic,
+                "kernel": (f"k_sweeps (fused: {sweeps_per_launch} sweeps per launch)" if fused
+                           else "k_phase (one half-sweep)"),
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (rate measured, profiles/fp64_peak.md)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
@@ -354,9 +379,7 @@ def run_mine(args):
                    "parallelism": f"replicas x{ws}" if ws > 1 else "1 GPU"},
         "gbs_per_sweep": sweep_bytes / (ms / args.steps * 1e-3) / 1e9,
         "roofline": roof,
-        "kernel_ms_per_sweep": {"half1": prof["half1_ms"] / prof_steps,
-                                "half2": prof["half2_ms"] / prof_steps,
-                                "normalise": prof["norm_ms"] / prof_steps},
+        "kernel_ms_per_sweep": kern_ms_per_sweep,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
                 "d2h_bytes_per_step": 8 * N + 8 * 3},
         "gpu_launches": prof["launches"],

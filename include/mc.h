@@ -178,8 +178,17 @@ int mc_factor(mc_chain* chain);
  *   nsweeps >= 1.
  *   stats_dev: NULL or device array of 3 doubles receiving, for the last
  *     sweep, [e^T z, ||x_new - x_old||_1, NaN] (the third slot is reserved).
+ * Block-tridiagonal chains with a stair splitting (desc.stair 1 or 2) run the
+ * nsweeps sweeps as one persistent launch per 1024 sweeps, with no
+ * normalisation between the sweeps of a launch (the scale of the iterate
+ * does not change the next one, Eq. (2) up to rounding); x_out is normalised
+ * and stats refer to the last sweep as above.  Results are bitwise
+ * reproducible for equal calls; a run split into several calls agrees up to
+ * rounding.
  * Async.  Errors: MC_ERR_ARG, MC_ERR_NOT_FACTORED, MC_ERR_CUDA; a breakdown
- * (e^T z <= 0 or not finite) is latched on the device (MC_ERR_BREAKDOWN).
+ * (e^T z <= 0 or not finite) is latched on the device (MC_ERR_BREAKDOWN);
+ * MC_ERR_TIMEOUT if a bounded device-side wait of the fused launch gave up
+ * (never expected: every wait is for work already claimed by a running warp).
  */
 int mc_sweep(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps,
              double* stats_dev);
@@ -193,11 +202,27 @@ int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, 
                   double* stats_host);
 
 /*
+ * Self-test of the bounded device-side wait used between the units of a fused
+ * sweep launch (no counterpart in the paper: it checks this library's
+ * guarantee that a wait which can never be satisfied ends with an error
+ * instead of hanging the GPU).  One warp waits for two completion counters
+ * that are set (reachable != 0) or never set (reachable == 0), for at most
+ * wait_ns nanoseconds (0 <= wait_ns <= 1e10).  Uses a small static device
+ * buffer (not thread-safe across concurrent calls).  Syncs cuda_stream.
+ * Returns MC_OK (reached) or MC_ERR_TIMEOUT (gave up), MC_ERR_ARG, MC_ERR_CUDA.
+ */
+int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns);
+
+/*
  * Diagnostics: exactly mc_sweep(x_in, x_out, nsweeps, NULL), with CUDA events
- * recorded on the handle's stream around each of the three kernel launches
- * of every sweep.  ms_host (4 doubles, host) receives the summed device time
- * in milliseconds of half-sweep 1, half-sweep 2 and the normalisation, and
- * the number of kernel launches.  1 <= nsweeps <= 2^20.  Syncs.
+ * recorded on the handle's stream.  ms_host (5 doubles, host) receives device
+ * times in milliseconds and the number of kernel launches:
+ *   fused stair sweeps (ms_host[4] = 1): [0] the fused sweep kernel(s) with
+ *     their counter reset, [1] the reduction of e^T z, [2] the normalisation,
+ *     [3] launches;
+ *   otherwise (ms_host[4] = 0): [0] half-sweep 1, [1] half-sweep 2, [2] the
+ *     normalisations, summed over the sweeps, [3] launches.
+ * 1 <= nsweeps <= 2^20.  Syncs.
  */
 int mc_profile(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps,
                double* ms_host);

@@ -71,6 +71,8 @@ def load():
     lib.mc_export.restype = ctypes.c_int
     lib.mc_residual_noalloc.argtypes = [vp, vp, vp, i64, i32, vp, vp, vp]
     lib.mc_residual_noalloc.restype = ctypes.c_int
+    lib.mc_wait_selftest.argtypes = [vp, i32, i64]
+    lib.mc_wait_selftest.restype = ctypes.c_int
     lib.mc_server_create.argtypes = [ctypes.POINTER(McServerDesc), vp, sz, vp, ctypes.POINTER(vp)]
     lib.mc_server_create.restype = ctypes.c_int
     lib.mc_server_request_bytes.argtypes = [vp, i64, i32]

@@ -99,10 +99,14 @@ class Chain:
         _need(x_in, (self.N,), "x_in")
         if x_out is None:
             x_out = torch.empty_like(x_in)
-        ms = (ctypes.c_double * 4)()
+        ms = (ctypes.c_double * 5)()
         nat.check(self._lib.mc_profile(self._h, _ptr(x_in), _ptr(x_out), int(nsweeps), ms),
                   "mc_profile")
-        return x_out, dict(half1_ms=ms[0], half2_ms=ms[1], norm_ms=ms[2], launches=int(ms[3]))
+        if ms[4] == 1.0:
+            return x_out, dict(fused=True, sweeps_ms=ms[0], scale_ms=ms[1], norm_ms=ms[2],
+                               launches=int(ms[3]))
+        return x_out, dict(fused=False, half1_ms=ms[0], half2_ms=ms[1], norm_ms=ms[2],
+                           launches=int(ms[3]))
 
     def sweep_host(self, x_in, x_out, nsweeps=1):
         """Host-buffer variant (x_in, x_out: CPU float64, ideally pinned)."""

@@ -58,6 +58,10 @@ Layout make_layout(const mc_desc& d) {
   o += round_up(kMaxNormBlocks * sizeof(double), 256);
   y.off_rpart = o;
   o += round_up(kMaxWarps * sizeof(double), 256);
+  y.off_fsum = o;
+  o += round_up((2 * (size_t)d.L + 2) * sizeof(double), 256);
+  y.off_fver = o;
+  o += round_up(sizeof(unsigned long long) + (size_t)d.L * sizeof(int), 256);
   y.lp = d.dtype == MC_F32 ? 1 : d.dtype == MC_BF16 ? 2 : 0;
   if (y.lp) {
     const size_t es = y.lp == 1 ? 4 : 2;
@@ -92,16 +96,12 @@ using namespace mc;
     if ((call) != cudaSuccess) return MC_ERR_CUDA; \
   } while (0)
 
-// Enqueue one sweep.  ev (optional) = 4 events recorded before half-sweep 1,
-// between the half-sweeps, before and after the normalisation.
-// mode: 0 = full sweep (normalise into dst with the step error);
-//       1 = unnormalised (z and e^T z only; dst untouched);
-//       2 = normalise into dst without the step error.
-// scaled_src: src is the unnormalised z of the previous sweep (mode 1), read
-// with the factor 1 / e^T z, which reproduces the stored normalised values.
+// Enqueue one sweep as separate launches (block-banded chains, block Jacobi /
+// Gauss-Seidel): the half-sweeps, then the normalisation into dst with the
+// step error.  ev (optional) = 4 events recorded before half-sweep 1, between
+// the half-sweeps, before and after the normalisation.
 static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* stats_out,
-                         cudaStream_t s, cudaEvent_t* ev = nullptr, int mode = 0,
-                         bool scaled_src = false) {
+                         cudaStream_t s, cudaEvent_t* ev = nullptr) {
   const int64_t L = c->lay.L;
   const int p1 = c->d.stair == 1 ? 0 : 1;   // 0-based parity of the diagonal-only rows
   const int p2 = 1 - p1;
@@ -115,7 +115,6 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.m = c->lay.m;
   a.ms = c->lay.ms;
   a.stride = 2;
-  a.s_prev = scaled_src ? &c->hdr->stats[0] : nullptr;
   a.far = c->lay.nfar ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
   a.xfar = src;
   if (c->d.stair >= 3) {
@@ -131,7 +130,6 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
     a.P = L;
     a.reduce_s = 1;
     a.n_wpart = c->nw;
-    a.paired = 0;
     if (ev) CK(cudaEventRecord(ev[0], s));
     if (c->d.stair == 3) {
       CK(launch_phase(a, coupled, c->nb_phase, s));
@@ -150,14 +148,11 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   a.hdr = c->hdr;
   a.reduce_s = 0;
   a.n_wpart = 2 * c->nw;
-  a.paired = c->d.paired && !coupled;
   if (ev) CK(cudaEventRecord(ev[0], s));
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[1], s));
-  // half-sweep 2: coupled rows read the fresh z of their neighbours (this
-  // sweep's own z: never rescaled)
+  // half-sweep 2: coupled rows read the fresh z of their neighbours
   a.src = c->z;
-  a.s_prev = nullptr;
   a.wpart = c->wpart + c->nw;
   a.parity = p2;
   a.P = (L - p2 + 1) / 2;
@@ -165,13 +160,9 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   CK(launch_phase(a, coupled, c->nb_phase, s));
   if (ev) CK(cudaEventRecord(ev[2], s));
   }
-  if (mode == 1) {
-    if (ev) CK(cudaEventRecord(ev[3], s));
-    return MC_OK;
-  }
   NormArgs n{};
   n.z = c->z;
-  n.x_old = mode == 0 ? src : nullptr;
+  n.x_old = src;
   n.x_new = dst;
   n.s = &c->hdr->stats[0];
   n.dpart = c->dpart;
@@ -183,28 +174,86 @@ static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* st
   return MC_OK;
 }
 
-// nsweeps sweeps src -> dst (in place allowed).  Sweeps 1..n-2 stay
-// unnormalised in z (the next sweep scales on read), sweep n-1 writes the
-// normalised iterate to dst, sweep n is a full sweep with the step error:
-// the iterates are bitwise those of n full sweeps, with two normalisation
-// passes instead of n.
+// Sweeps per fused launch: bounds the launch and keeps the unnormalised
+// iterates of one launch far from the FP64 range limits.
+constexpr int64_t kMaxFusedSweeps = 1024;
+// Bound of one wait for a neighbour level in a fused launch.  A wait is for a
+// unit that a running warp has already claimed, normally well under a
+// millisecond even at m = 256; two seconds only catches a broken invariant.
+constexpr unsigned long long kFusedWaitNs = 2000000000ull;
+
+static bool fused_ok(const mc_chain* c) { return c->d.stair <= 2 && c->lay.nfar == 0; }
+
+// n stair sweeps src -> dst (in place allowed) as fused launches of at most
+// kMaxFusedSweeps sweeps, each followed by the normalisation (with the step
+// error after the last).  ev (optional, 4 events): before the first launch,
+// after the last fused kernel, after its scale reduction, after the last
+// normalisation.
+static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int64_t n,
+                                double* stats_out, cudaStream_t s, cudaEvent_t* ev) {
+  const bool coupled = c->d.apply == MC_APPLY_COUPLED;
+  const size_t pe = c->lay.plane_bytes / sizeof(double);
+  const int64_t L = c->lay.L;
+  const size_t cnt_bytes = sizeof(unsigned long long) + (size_t)L * sizeof(int);
+  double* scale = c->flsum + 2 * L;
+  if (ev) CK(cudaEventRecord(ev[0], s));
+  const double* in = src;
+  for (int64_t done = 0; done < n;) {
+    const int64_t K = n - done < kMaxFusedSweeps ? n - done : kMaxFusedSweeps;
+    const bool final = done + K == n;
+    FusedArgs a{};
+    a.A = c->planes + (coupled ? kPlaneWLO : kPlaneTLO) * pe;
+    a.B = c->planes + (coupled ? kPlaneWUP : kPlaneTUP) * pe;
+    a.C = c->planes + kPlaneNINV * pe;
+    a.x_in = in;
+    a.W = c->xb;
+    a.Z = c->z;
+    a.lsum = c->flsum;
+    a.ver = c->fver;
+    a.claim = c->fclaim;
+    a.hdr = c->hdr;
+    a.L = L;
+    a.K = K;
+    a.par0 = c->d.stair == 1 ? 0 : 1;
+    a.P0 = (L - a.par0 + 1) / 2;
+    a.m = c->lay.m;
+    a.ms = c->lay.ms;
+    a.paired = c->d.paired && !coupled;
+    a.wait_ns = kFusedWaitNs;
+    CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
+    CK(launch_sweeps_fused(a, coupled, c->nb_fused, s));
+    if (ev && final) CK(cudaEventRecord(ev[1], s));
+    CK(launch_fused_scale(c->flsum, L, K, scale, s));
+    if (ev && final) CK(cudaEventRecord(ev[2], s));
+    NormArgs nn{};
+    nn.z = c->z;
+    // step error of the last sweep: z_K / s_K against z_{K-1} / s_{K-1}
+    nn.x_old = final ? (K == 1 ? in : c->xb) : nullptr;
+    nn.s_old = scale + 1;
+    nn.x_new = dst;
+    nn.s = scale;
+    nn.dpart = c->dpart;
+    nn.hdr = c->hdr;
+    nn.stats_out = final ? stats_out : nullptr;
+    nn.N = c->lay.N;
+    CK(launch_normalise(nn, c->nb_norm, s));
+    in = dst;
+    done += K;
+  }
+  if (ev) CK(cudaEventRecord(ev[3], s));
+  return MC_OK;
+}
+
+// nsweeps sweeps src -> dst (in place allowed).  Stair splittings of
+// block-tridiagonal chains run as fused launches; block-banded chains (whose
+// far terms read the previous iterate in both half-sweeps) and the comparison
+// splittings run one sweep at a time, each normalised.
 static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
                           double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr) {
-  // (block-banded chains read x for the far terms of both half-sweeps, so
-  // the previous iterate must be stored)
-  const bool lagged = c->d.stair <= 2 && n > 2 && c->lay.nfar == 0;
+  if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev);
   for (int64_t k = 0; k < n; ++k) {
-    cudaEvent_t* e = ev ? ev + 4 * k : nullptr;
-    int rc;
-    if (!lagged) {
-      rc = enqueue_sweep(c, k == 0 ? src : dst, dst, k == n - 1 ? stats_out : nullptr, s, e);
-    } else if (k < n - 2) {
-      rc = enqueue_sweep(c, k == 0 ? src : c->z, dst, nullptr, s, e, 1, k > 0);
-    } else if (k == n - 2) {
-      rc = enqueue_sweep(c, c->z, dst, nullptr, s, e, 2, true);
-    } else {
-      rc = enqueue_sweep(c, dst, dst, stats_out, s, e, 0, false);
-    }
+    const int rc = enqueue_sweep(c, k == 0 ? src : dst, dst, k == n - 1 ? stats_out : nullptr, s,
+                                 ev ? ev + 4 * k : nullptr);
     if (rc != MC_OK) return rc;
   }
   return MC_OK;
@@ -326,6 +375,9 @@ int mc::chain_init(const mc_desc* desc, void* workspace, size_t ws_bytes, cudaSt
   c->wpart = (double*)(c->ws + lay.off_wpart);
   c->dpart = (double*)(c->ws + lay.off_dpart);
   c->rpart = (double*)(c->ws + lay.off_rpart);
+  c->flsum = (double*)(c->ws + lay.off_fsum);
+  c->fclaim = (unsigned long long*)(c->ws + lay.off_fver);
+  c->fver = (int*)(c->ws + lay.off_fver + sizeof(unsigned long long));
   // persistent grids: the full resident grid of the kernel's occupancy (a
   // multiple of the SM count) once there is at least one unit per SM, else one
   // warp per unit
@@ -340,6 +392,11 @@ int mc::chain_init(const mc_desc* desc, void* workspace, size_t ws_bytes, cudaSt
   if (lay.L < sms) wr = lay.L;
   if (wr > kMaxWarps) wr = kMaxWarps;
   c->nb_resid = (int)((wr + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  // fused launches claim units dynamically: the full resident grid, but no
+  // more warps than levels
+  int64_t wf = wps * sms;
+  if (wf > lay.L) wf = lay.L;
+  c->nb_fused = (int)((wf + kWarpsPerBlock - 1) / kWarpsPerBlock);
   int64_t nbn = (lay.N + 4 * kNormThreads - 1) / (4 * kNormThreads);
   if (nbn > 8 * sms) nbn = 8 * sms;
   if (nbn > kMaxNormBlocks) nbn = kMaxNormBlocks;
@@ -478,7 +535,8 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   if (!c || !x_in || !x_out || !ms_host || nsweeps < 1 || nsweeps > (1 << 20)) return MC_ERR_ARG;
   if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
-  const size_t ne = 4 * (size_t)nsweeps;
+  const bool fused = !c->lay.lp && fused_ok(c);
+  const size_t ne = fused ? 4 : 4 * (size_t)nsweeps;
   cudaEvent_t* ev = (cudaEvent_t*)calloc(ne, sizeof(cudaEvent_t));
   if (!ev) return MC_ERR_ARG;
   int rc = MC_OK;
@@ -504,7 +562,7 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   }
   double t[3] = {0.0, 0.0, 0.0};
   if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
-  for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k)
+  for (int64_t k = 0; k < (fused ? 1 : nsweeps) && rc == MC_OK; ++k)
     for (int q = 0; q < 3; ++q) {
       float ms = 0.0f;
       if (cudaEventElapsedTime(&ms, ev[4 * k + q], ev[4 * k + q + 1]) != cudaSuccess) {
@@ -519,11 +577,15 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   ms_host[0] = t[0];
   ms_host[1] = t[1];
   ms_host[2] = t[2];
-  // kernel launches: 2 per sweep (1 for the comparison splittings) plus the
-  // normalisations (1 per sweep unless the lagged scheme keeps them to 2)
-  const bool lagged = !c->lay.lp && c->d.stair <= 2 && nsweeps > 2 && c->lay.nfar == 0;
+  // kernel launches: fused chains 3 per launch of up to kMaxFusedSweeps
+  // sweeps (sweeps, scale, normalisation); otherwise 2 per sweep (1 for the
+  // comparison splittings) plus one normalisation per sweep
   const double per = c->lay.lp ? 2.0 : (c->d.stair <= 2 ? 2.0 : 1.0);
-  ms_host[3] = per * (double)nsweeps + (c->lay.lp ? 1.0 : (lagged ? 2.0 : (double)nsweeps));
+  if (fused)
+    ms_host[3] = 3.0 * (double)((nsweeps + kMaxFusedSweeps - 1) / kMaxFusedSweeps);
+  else
+    ms_host[3] = per * (double)nsweeps + (c->lay.lp ? 1.0 : (double)nsweeps);
+  ms_host[4] = fused ? 1.0 : 0.0;
   return sync_header(c);
 }
 

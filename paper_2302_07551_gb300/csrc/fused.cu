@@ -1,0 +1,230 @@
+// Several staircase sweeps (Algorithm 2, repeated) in one persistent launch.
+//
+// Work units are (sweep k, half-sweep h, level l), claimed in that order from
+// one queue counter.  Half-sweep 1 of sweep k (the diagonal-only stair rows)
+// reads its neighbours as left by half-sweep 2 of sweep k-1; half-sweep 2
+// reads its neighbours as left by half-sweep 1 of sweep k.  So each unit
+// depends on exactly two earlier units, the neighbour levels l-1 and l+1, and
+// waits for them through per-level completion counters instead of a launch
+// boundary: the grid streams through all K sweeps with one ramp-up and one
+// tail, and the queue balances the load across warps and SMs.
+//
+// The vector is updated in place (W).  A unit overwrites level l only after
+// both units that read the old value of level l (its neighbours' previous
+// updates) have completed, which is exactly the condition it waits for.  The
+// last sweep writes Z instead, so that W keeps z_{K-1} for the step error.
+//
+// Progress: a warp handles its claimed units in increasing queue order and
+// every unit depends only on units earlier in the queue, all claimed by
+// running warps, so the earliest unfinished unit can always proceed.  Each
+// wait is still bounded (FusedArgs::wait_ns of the GPU's global timer); on
+// expiry the warp latches MC_ERR_TIMEOUT and carries on, so the launch
+// always ends.
+//
+// Values and level sums do not depend on which warp handles which unit, and
+// the sums are reduced per level in a fixed order: results are bitwise
+// reproducible for any grid.
+#include <math.h>
+
+#include "mc_internal.cuh"
+#include "sweep_dev.cuh"
+
+namespace mc {
+
+namespace {
+
+using namespace dev;
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Wait until levels l-1 and l+1 (where they exist) have completed `need`
+// writes in this launch, for at most wait_ns nanoseconds.  Lane 0 polls; then
+// every lane performs its own acquire of both counters, which orders its
+// reads of the neighbour vectors after the producers' writes.
+__device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64_t L, int need,
+                                                Header* hdr, int lane,
+                                                unsigned long long wait_ns) {
+  const bool lo = l > 0, up = l < L - 1;
+  if (lane == 0) {
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+      const bool ok = (!lo || ld_acquire(ver + l - 1) >= need) &&
+                      (!up || ld_acquire(ver + l + 1) >= need);
+      if (ok) break;
+      if (it == 0) {
+        t0 = global_ns();
+      } else if (global_ns() - t0 > wait_ns) {
+        latch(hdr, MC_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncwarp();
+  if (lo) (void)ld_acquire(ver + l - 1);
+  if (up) (void)ld_acquire(ver + l + 1);
+}
+
+// Level l now holds its version v: every lane's stores of z_l are made
+// visible before the counter.
+__device__ __forceinline__ void publish(int* ver, int v, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane == 0) st_release(ver, v);
+}
+
+template <int R, bool COUPLED, bool PAIRED>
+__global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
+  extern __shared__ double vsh[];
+  const int lane = threadIdx.x & 31;
+  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
+  const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
+  unsigned long long q0 = lane == 0 ? atomicAdd(a.claim, 1ull) : 0ull;
+  unsigned long long q = __shfl_sync(kFull, q0, 0);
+  while (q < total) {
+    // claim the next unit now; its index is needed only after this one
+    q0 = lane == 0 ? atomicAdd(a.claim, 1ull) : 0ull;
+    const int64_t k = (int64_t)(q / (unsigned long long)a.L);
+    const int64_t r = (int64_t)q - k * a.L;
+    const bool h2 = r >= a.P0;
+    const int64_t l = h2 ? 2 * (r - a.P0) + (1 - a.par0) : 2 * r + a.par0;
+    const bool last = k == a.K - 1;
+    double* dst = last ? a.Z : a.W;
+    // half-sweep 1 reads z_k (x_in for k = 0); half-sweep 2 reads z_{k+1}
+    const double* src = h2 ? dst : (k == 0 ? a.x_in : a.W);
+    const int need = (int)(h2 ? k + 1 : k);
+    if (need > 0) wait_neighbours(a.ver, l, a.L, need, a.hdr, lane, a.wait_ns);
+    const double t = level_sweep2<R, COUPLED, PAIRED, true, true>(
+        a.A, a.B, a.C, src, src, dst, l, a.L, a.m, a.ms, slice, lane);
+    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+    publish(a.ver + l, (int)(k + 1), lane);
+    q = __shfl_sync(kFull, q0, 0);
+  }
+}
+
+// Self-test of the bounded wait: one warp waits for level 1 of a 3-level
+// counter array; the counters hold `preset`, the wait needs 1.
+__global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver) {
+  const int lane = threadIdx.x & 31;
+  if (lane < 3) ver[lane] = preset;
+  __syncwarp();
+  wait_neighbours(ver, 1, 3, 1, hdr, lane, wait_ns);
+}
+
+// e^T z_K and e^T z_{K-1} from the per-level sums (one block, fixed order).
+__global__ void __launch_bounds__(1024) k_fused_scale(const double* lsum, int64_t L, int64_t K,
+                                                      double* out) {
+  __shared__ double sh[32];
+  const double* a = lsum + ((K - 1) & 1) * L;
+  const double* b = lsum + ((K - 2) & 1) * L;
+  double ta = 0.0, tb = 0.0;
+  for (int64_t l = threadIdx.x; l < L; l += blockDim.x) {
+    ta += a[l];
+    if (K >= 2) tb += b[l];
+  }
+  ta = block_sum(ta, sh);
+  tb = block_sum(tb, sh);
+  if (threadIdx.x == 0) {
+    out[0] = ta;
+    out[1] = K >= 2 ? tb : 1.0;
+  }
+}
+
+template <int R, bool C, bool P = false>
+cudaError_t sweeps_r(const FusedArgs& a, int nb, cudaStream_t s) {
+  static bool done = false;
+  const size_t smem = (size_t)kWarpsPerBlock * 3 * 32 * R * sizeof(double);
+  if (!done && smem > 40 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_sweeps<R, C, P>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  k_sweeps<R, C, P><<<nb, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+template <bool C>
+cudaError_t sweeps_dispatch(const FusedArgs& a, int nb, cudaStream_t s) {
+  if (a.paired && !C) {
+    switch (a.m / 32) {
+      case 2: return sweeps_r<2, false, true>(a, nb, s);
+      case 4: return sweeps_r<4, false, true>(a, nb, s);
+      case 6: return sweeps_r<6, false, true>(a, nb, s);
+      case 8: return sweeps_r<8, false, true>(a, nb, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch ((a.m + 31) / 32) {
+    case 1: return sweeps_r<1, C>(a, nb, s);
+    case 2: return sweeps_r<2, C>(a, nb, s);
+    case 3: return sweeps_r<3, C>(a, nb, s);
+    case 4: return sweeps_r<4, C>(a, nb, s);
+    case 5: return sweeps_r<5, C>(a, nb, s);
+    case 6: return sweeps_r<6, C>(a, nb, s);
+    case 7: return sweeps_r<7, C>(a, nb, s);
+    case 8: return sweeps_r<8, C>(a, nb, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_sweeps_fused(const FusedArgs& a, int coupled, int n_blocks, cudaStream_t s) {
+  return coupled ? sweeps_dispatch<true>(a, n_blocks, s) : sweeps_dispatch<false>(a, n_blocks, s);
+}
+
+cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver,
+                                 cudaStream_t s) {
+  k_wait_selftest<<<1, 32, 0, s>>>(preset, wait_ns, hdr, ver);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
+                               cudaStream_t s) {
+  k_fused_scale<<<1, 1024, 0, s>>>(lsum, L, K, out);
+  return cudaGetLastError();
+}
+
+}  // namespace mc
+
+namespace {
+struct WaitSelftestScratch {
+  mc::Header hdr;
+  int ver[4];
+};
+__device__ __align__(256) WaitSelftestScratch g_wait_selftest;
+}  // namespace
+
+extern "C" int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns) {
+  if (wait_ns < 0 || wait_ns > 10000000000ll) return MC_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)cuda_stream;
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_wait_selftest) != cudaSuccess || !p) return MC_ERR_CUDA;
+  WaitSelftestScratch* w = (WaitSelftestScratch*)p;
+  if (cudaMemsetAsync(w, 0, sizeof(WaitSelftestScratch), s) != cudaSuccess) return MC_ERR_CUDA;
+  if (mc::launch_wait_selftest(reachable ? 1 : 0, (unsigned long long)wait_ns, &w->hdr, w->ver,
+                               s) != cudaSuccess)
+    return MC_ERR_CUDA;
+  int status = 0;
+  if (cudaMemcpyAsync(&status, &w->hdr.status, sizeof(int), cudaMemcpyDeviceToHost, s) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return MC_ERR_CUDA;
+  return status;
+}

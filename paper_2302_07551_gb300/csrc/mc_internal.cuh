@@ -11,6 +11,8 @@
 //              of mc_solve / mc_sweep), each N doubles rounded to 32.
 //   [partials] per-warp level-sum partials of the two half-sweeps, per-block
 //              step-error partials, per-warp residual partials.
+//   [fused]    per-level sums of the last two sweeps and the queue / per-level
+//              counters of the fused multi-sweep launch.
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -54,6 +56,9 @@ struct Layout {
   int far_base;          // plane index of the first far diagonal
   size_t plane_bytes, vec_bytes;
   size_t off_hdr, off_planes, off_z, off_xa, off_xb, off_wpart, off_dpart, off_rpart, total;
+  // fused multi-sweep launches: per-level sums of the last two sweeps (+ the
+  // two scales), queue counter + per-level completion counters
+  size_t off_fsum, off_fver;
   // low-precision storage (dtype MC_F32 / MC_BF16)
   int lp;                // 0: none, 1: FP32, 2: BF16
   int64_t lp_bs;         // elements per stored block of the A/B planes
@@ -70,7 +75,6 @@ struct PhaseArgs {
   const double* C;       // NINV plane (inverse mode), unused when coupled
   const double* src;     // vector read at neighbour levels l-1, l+1
   const double* src_up;  // if set: vector read at level l+1 instead (block Gauss-Seidel)
-  const double* s_prev;  // if set: src is an unnormalised z, scaled by 1 / *s_prev on read
   const FarDesc* far;    // if set: off-staircase diagonals, read from xfar
   const double* xfar;    // the sweep's input x (far terms of both half-sweeps)
   double* dst;           // z, written at this half-sweep's levels
@@ -82,12 +86,38 @@ struct PhaseArgs {
   int stride;            // 2: stair half-sweep, 1: all levels (block Jacobi)
   int reduce_s;          // last block sums the n_wpart partials into hdr->stats[0]
   int n_wpart;           // partials of both half-sweeps (reduce_s only)
-  int paired;            // skip the zero quadrants of a paired pentadiagonal chain
+};
+
+// Several sweeps in one persistent launch (Algorithm 2 repeated K times):
+// the units (sweep k, half-sweep h, level l) are claimed in that order from a
+// queue counter; a unit waits until its two neighbour levels hold the values
+// it reads (per-level completion counters), so no launch boundary or grid
+// barrier separates half-sweeps or sweeps.  The sweeps are not normalised in
+// between: z_{k+1} = M^{-1} N z_k, z_0 = x_in; e^T z of the last two sweeps is
+// kept per level for the final normalisation.
+struct FusedArgs {
+  const double* A;       // TLO / WLO plane
+  const double* B;       // TUP / WUP plane
+  const double* C;       // NINV plane (inverse mode)
+  const double* x_in;    // z_0 (read by the first half-sweep only)
+  double* W;             // z_1 .. z_{K-1}, in place
+  double* Z;             // z_K
+  double* lsum;          // [2][L]: e^T of level l of sweep k in slot k & 1
+  int* ver;              // [L]: completed writes of level l in this launch (zeroed before)
+  unsigned long long* claim;   // queue position (zeroed before)
+  Header* hdr;
+  int64_t L, K;          // levels, sweeps
+  int64_t P0;            // levels of half-sweep 1 (parity par0)
+  int m, ms;
+  int par0;              // 0: STAIR1, 1: STAIR2
+  int paired;
+  unsigned long long wait_ns;   // bound of one wait for a neighbour level
 };
 
 struct NormArgs {
   const double* z;
   const double* x_old;   // NULL: no step error (the previous iterate was not stored)
+  const double* s_old;   // NULL: x_old is normalised; else x_old / *s_old is the iterate
   double* x_new;
   const double* s;       // e^T z (hdr->stats[0], written by half-sweep 2)
   double* dpart;         // one per block
@@ -127,6 +157,14 @@ cudaError_t launch_phase(const PhaseArgs& a, int coupled, int n_blocks, cudaStre
 cudaError_t launch_bgs(const PhaseArgs& a, int coupled, cudaStream_t s);
 int phase_blocks_per_sm(int m);   // resident 256-thread blocks of k_phase per SM
 cudaError_t launch_normalise(const NormArgs& a, int n_blocks, cudaStream_t s);
+cudaError_t launch_sweeps_fused(const FusedArgs& a, int coupled, int n_blocks, cudaStream_t s);
+// One warp waits (at most wait_ns) for counters preset to `preset` to reach 1;
+// MC_ERR_TIMEOUT is latched in hdr when they never do.
+cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver,
+                                 cudaStream_t s);
+// out[0] = e^T z_K, out[1] = e^T z_{K-1} (1 when K = 1), fixed summation order.
+cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
+                               cudaStream_t s);
 cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
 // Latch MC_ERR_ARG unless the paired zero quadrants of TLO / TUP are zero.

@@ -44,11 +44,10 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   const int nw = (int)((gridDim.x * blockDim.x) >> 5);
   const int gw = sched_warp(a.P, nw);
   double wsum = 0.0;
-  const double scale = a.s_prev ? 1.0 / *a.s_prev : 1.0;
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = a.stride * u + a.parity;
     wsum += level_sweep2<R, COUPLED, PAIRED, false>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L,
-                                                    a.m, a.ms, slice, lane, scale, a.far, a.xfar,
+                                                    a.m, a.ms, slice, lane, 1.0, a.far, a.xfar,
                                                     a.xfar);
   }
   wsum = warp_sum(wsum);   // the lanes' partials over all of this warp's levels
@@ -98,6 +97,8 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   const bool ok = (s > 0.0) && isfinite(s);
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) latch(a.hdr, MC_ERR_BREAKDOWN);
   const double inv = 1.0 / s;
+  const double so = a.s_old ? *a.s_old : 1.0;
+  const double pinv = 1.0 / so;   // exactly 1 for a normalised x_old
   double d = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool vec = ((((uintptr_t)a.x_old) | ((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0;
@@ -114,19 +115,19 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
       double2 p;
       p.x = zz.x * inv;
       p.y = zz.y * inv;
-      d += fabs(p.x - xx.x) + fabs(p.y - xx.y);
+      d += fabs(p.x - xx.x * pinv) + fabs(p.y - xx.y * pinv);
       y2[i] = p;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.N & 1)) {
       const int64_t i = a.N - 1;
       const double p = a.z[i] * inv;
-      d += fabs(p - a.x_old[i]);
+      d += fabs(p - a.x_old[i] * pinv);
       a.x_new[i] = p;
     }
   } else {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride) {
       const double p = a.z[i] * inv;
-      d += fabs(p - a.x_old[i]);
+      d += fabs(p - a.x_old[i] * pinv);
       a.x_new[i] = p;
     }
   }
@@ -144,10 +145,13 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
     for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) e += __ldcg(a.dpart + i);
     e = block_sum(e, sh);
     if (threadIdx.x == 0) {
+      // e^T z relative to the previous iterate (s itself when that was normalised)
+      const double sr = s / so;
+      a.hdr->stats[0] = sr;
       a.hdr->stats[1] = e;
       a.hdr->stats[2] = nan("");
       if (a.stats_out) {
-        a.stats_out[0] = s;
+        a.stats_out[0] = sr;
         a.stats_out[1] = e;
         a.stats_out[2] = nan("");
       }
@@ -248,15 +252,6 @@ cudaError_t phase_r(const PhaseArgs& a, int nb, cudaStream_t s) {
 
 template <bool C>
 cudaError_t phase_dispatch(const PhaseArgs& a, int nb, cudaStream_t s) {
-  if (a.paired && !C) {
-    switch (a.m / 32) {
-      case 2: return phase_r<2, false, true>(a, nb, s);
-      case 4: return phase_r<4, false, true>(a, nb, s);
-      case 6: return phase_r<6, false, true>(a, nb, s);
-      case 8: return phase_r<8, false, true>(a, nb, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
   switch ((a.m + 31) / 32) {
     case 1: return phase_r<1, C>(a, nb, s);
     case 2: return phase_r<2, C>(a, nb, s);

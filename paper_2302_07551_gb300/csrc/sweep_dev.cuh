@@ -122,20 +122,22 @@ __device__ __forceinline__ void gemv_up_paired(double (&acc)[R][Tune<R>::NA],
 // v = p * scale (scale = 1 / e^T z of the previous sweep when the previous
 // sweep was not normalised in memory; 1 otherwise: fl(z * (1/s)) is exactly
 // the value the normalisation would have stored).
-template <int R>
+// CG: p was written by other SMs during this kernel, so it is read from L2
+// (ld.global.cg), never from a possibly stale L1 line.
+template <int R, bool CG = false>
 __device__ __forceinline__ void stage_vec(double* v, const double* __restrict__ p, int m,
                                           int lane, double scale = 1.0) {
   if (scale != 1.0) {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int row = lane + 32 * r;
-      v[row] = row < m ? p[row] * scale : 0.0;
+      v[row] = row < m ? (CG ? __ldcg(p + row) : p[row]) * scale : 0.0;
     }
   } else {
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       const int row = lane + 32 * r;
-      v[row] = row < m ? p[row] : 0.0;
+      v[row] = row < m ? (CG ? __ldcg(p + row) : p[row]) : 0.0;
     }
   }
 }
@@ -194,7 +196,8 @@ __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const F
 
 // Returns sum_i z_l[i]: on every lane (WARP_TOTAL) or the lane's own rows
 // only (callers that only need a total over many levels reduce once at the end).
-template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true>
+// CG: neighbour vectors written by other SMs during this kernel (L2 reads).
+template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true, bool CG = false>
 __device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
                                                const double* src, const double* src_up,
                                                double* dst, int64_t l, int64_t L, int m, int ms,
@@ -207,8 +210,8 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
   double* v_up = slice + W;
   double* v_g = slice + 2 * W;
   const bool has_lo = l > 0, has_up = l < L - 1;
-  if (has_lo) stage_vec<R>(v_lo, src + (l - 1) * m, m, lane, scale);
-  if (has_up) stage_vec<R>(v_up, src_up + (l + 1) * m, m, lane, scale);
+  if (has_lo) stage_vec<R, CG>(v_lo, src + (l - 1) * m, m, lane, scale);
+  if (has_up) stage_vec<R, CG>(v_up, src_up + (l + 1) * m, m, lane, scale);
   __syncwarp();
   double acc[R][NA];
   zero_acc<R>(acc);
