@@ -364,7 +364,9 @@ def run_mine(args):
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": None,
-                "kernel": "k_phase_lp (one correction half-sweep)", "peak_source": hbm_src}
+                "kernel": (f"k_sweeps_lp (fused: {sweeps_per_launch} correction sweeps per launch)"
+                           if fused else "k_phase_lp (one correction half-sweep)"),
+                "peak_source": hbm_src}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,

@@ -214,12 +214,15 @@ int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, 
 int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns);
 
 /*
- * Diagnostics: exactly mc_sweep(x_in, x_out, nsweeps, NULL), with CUDA events
- * recorded on the handle's stream.  ms_host (5 doubles, host) receives device
- * times in milliseconds and the number of kernel launches:
- *   fused stair sweeps (ms_host[4] = 1): [0] the fused sweep kernel(s) with
- *     their counter reset, [1] the reduction of e^T z, [2] the normalisation,
- *     [3] launches;
+ * Diagnostics: for FP64 chains exactly mc_sweep(x_in, x_out, nsweeps, NULL);
+ * for low-precision chains (MC_F32 / MC_BF16) the correction sweeps of one
+ * refinement step from x_in (r and q of x_in, then nsweeps correction sweeps
+ * from d = 0 in one fused launch; x_out = x_in).  CUDA events are recorded on
+ * the handle's stream; ms_host (5 doubles, host) receives device times in
+ * milliseconds and the number of kernel launches:
+ *   fused sweeps (ms_host[4] = 1): [0] the fused sweep kernel(s) with their
+ *     counter reset, [1] the reduction of e^T z, [2] the normalisation (both
+ *     0 for low-precision chains), [3] launches;
  *   otherwise (ms_host[4] = 0): [0] half-sweep 1, [1] half-sweep 2, [2] the
  *     normalisations, summed over the sweeps, [3] launches.
  * 1 <= nsweeps <= 2^20.  Syncs.

@@ -59,7 +59,7 @@ Layout make_layout(const mc_desc& d) {
   y.off_rpart = o;
   o += round_up(kMaxWarps * sizeof(double), 256);
   y.off_fsum = o;
-  o += round_up((2 * (size_t)d.L + 2) * sizeof(double), 256);
+  o += round_up((2 * (size_t)d.L + 2 + 2 * kScaleBlocks) * sizeof(double), 256);
   y.off_fver = o;
   o += round_up(sizeof(unsigned long long) + (size_t)d.L * sizeof(int), 256);
   y.lp = d.dtype == MC_F32 ? 1 : d.dtype == MC_BF16 ? 2 : 0;
@@ -223,7 +223,7 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
     CK(launch_sweeps_fused(a, coupled, c->nb_fused, s));
     if (ev && final) CK(cudaEventRecord(ev[1], s));
-    CK(launch_fused_scale(c->flsum, L, K, scale, s));
+    CK(launch_fused_scale(c->flsum, L, K, scale, scale + 2, &c->hdr->ticket[4], s));
     if (ev && final) CK(cudaEventRecord(ev[2], s));
     NormArgs nn{};
     nn.z = c->z;
@@ -289,28 +289,23 @@ static float* lpQ(mc_chain* c) { return (float*)(c->ws + c->lay.off_q); }
 static float* lpD(mc_chain* c) { return (float*)(c->ws + c->lay.off_d); }
 
 // One correction sweep d <- M^{-1}(N d - r) in low precision (two launches).
-static int enqueue_lp_sweep(mc_chain* c, cudaStream_t s, cudaEvent_t* ev = nullptr) {
-  const int p1 = c->d.stair == 1 ? 0 : 1;
-  const int bf16 = c->lay.lp == 2, coupled = c->d.apply == MC_APPLY_COUPLED;
-  if (ev) CK(cudaEventRecord(ev[0], s));
-  CK(launch_phase_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m, p1,
-                     c->lay.lp_bs, c->lay.lp_cbs, bf16, coupled, c->nb_phase, s));
-  if (ev) CK(cudaEventRecord(ev[1], s));
-  CK(launch_phase_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m, 1 - p1,
-                     c->lay.lp_bs, c->lay.lp_cbs, bf16, coupled, c->nb_phase, s));
-  if (ev) CK(cudaEventRecord(ev[2], s));
-  return MC_OK;
-}
-
 // One outer step on the iterate xa: `inner` correction sweeps from d = 0 (q
 // must hold (-T_dd)^{-1} r for the current xa), pi <- (pi + d)/e^T(pi + d)
 // with the step error, then r and q of the new iterate.
+static int enqueue_lp_sweeps_fused(mc_chain* c, int64_t K, cudaStream_t s) {
+  const size_t cnt_bytes = sizeof(unsigned long long) + (size_t)c->lay.L * sizeof(int);
+  CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
+  CK(launch_sweeps_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m,
+                      c->d.stair == 1 ? 0 : 1, c->lay.lp_bs, c->lay.lp_cbs, c->lay.lp == 2,
+                      c->d.apply == MC_APPLY_COUPLED, K, c->fver, c->fclaim, c->hdr, kFusedWaitNs,
+                      c->nb_fused, s));
+  return MC_OK;
+}
+
 static int enqueue_refine_step(mc_chain* c, int inner, cudaStream_t s) {
   CK(cudaMemsetAsync(lpD(c), 0, (size_t)c->lay.N * sizeof(float), s));
-  for (int k = 0; k < inner; ++k) {
-    const int rc = enqueue_lp_sweep(c, s);
-    if (rc != MC_OK) return rc;
-  }
+  const int rc = enqueue_lp_sweeps_fused(c, inner, s);
+  if (rc != MC_OK) return rc;
   double* bpart = (double*)(c->ws + c->lay.off_bpart);
   CK(launch_update(c->xa, lpD(c), c->xb, c->lay.N, bpart, c->nb_norm, c->hdr, &c->hdr->stats[0],
                    s));
@@ -535,7 +530,8 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   if (!c || !x_in || !x_out || !ms_host || nsweeps < 1 || nsweeps > (1 << 20)) return MC_ERR_ARG;
   if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
-  const bool fused = !c->lay.lp && fused_ok(c);
+  // low-precision chains: the correction sweeps of refinement, always fused
+  const bool fused = c->lay.lp || fused_ok(c);
   const size_t ne = fused ? 4 : 4 * (size_t)nsweeps;
   cudaEvent_t* ev = (cudaEvent_t*)calloc(ne, sizeof(cudaEvent_t));
   if (!ev) return MC_ERR_ARG;
@@ -553,10 +549,10 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
                         c->user) != cudaSuccess)
       rc = MC_ERR_CUDA;
     if (rc == MC_OK) rc = enqueue_residual(c, c->xa, c->user, lpQ(c));
-    for (int64_t k = 0; k < nsweeps && rc == MC_OK; ++k) {
-      rc = enqueue_lp_sweep(c, c->user, ev + 4 * k);
-      if (rc == MC_OK && cudaEventRecord(ev[4 * k + 3], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
-    }
+    if (rc == MC_OK && cudaEventRecord(ev[0], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+    if (rc == MC_OK) rc = enqueue_lp_sweeps_fused(c, nsweeps, c->user);
+    for (int q = 1; q < 4 && rc == MC_OK; ++q)
+      if (cudaEventRecord(ev[q], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
   } else {
     rc = enqueue_sweeps(c, x_in, x_out, nsweeps, nullptr, c->user, ev);
   }
@@ -580,11 +576,13 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   // kernel launches: fused chains 3 per launch of up to kMaxFusedSweeps
   // sweeps (sweeps, scale, normalisation); otherwise 2 per sweep (1 for the
   // comparison splittings) plus one normalisation per sweep
-  const double per = c->lay.lp ? 2.0 : (c->d.stair <= 2 ? 2.0 : 1.0);
-  if (fused)
+  const double per = c->d.stair <= 2 ? 2.0 : 1.0;
+  if (c->lay.lp)
+    ms_host[3] = 2.0;   // residual (r, q) + the fused correction sweeps
+  else if (fused)
     ms_host[3] = 3.0 * (double)((nsweeps + kMaxFusedSweeps - 1) / kMaxFusedSweeps);
   else
-    ms_host[3] = per * (double)nsweeps + (c->lay.lp ? 1.0 : (double)nsweeps);
+    ms_host[3] = per * (double)nsweeps + (double)nsweeps;
   ms_host[4] = fused ? 1.0 : 0.0;
   return sync_header(c);
 }

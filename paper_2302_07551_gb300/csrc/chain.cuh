@@ -16,7 +16,7 @@ struct mc_chain {
   mc::Header* hdr;           // device header inside the workspace
   mc::Header* hh;            // pinned host copy of the header
   double *planes, *z, *xa, *xb, *wpart, *dpart, *rpart;
-  double* flsum;             // fused launches: [2][L] level sums, then 2 scales
+  double* flsum;             // fused launches: [2][L] level sums, 2 scales, block partials
   int* fver;                 // [L] completion counters, after the queue counter
   unsigned long long* fclaim;
   int nb_fused;              // grid of the fused multi-sweep kernel

@@ -28,6 +28,7 @@
 
 #include "mc_internal.cuh"
 #include "sweep_dev.cuh"
+#include "wave_dev.cuh"
 
 namespace mc {
 
@@ -35,69 +36,17 @@ namespace {
 
 using namespace dev;
 
-__device__ __forceinline__ int ld_acquire(const int* p) {
-  int v;
-  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-
-__device__ __forceinline__ void st_release(int* p, int v) {
-  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-// Wait until levels l-1 and l+1 (where they exist) have completed `need`
-// writes in this launch, for at most wait_ns nanoseconds.  Lane 0 polls; then
-// every lane performs its own acquire of both counters, which orders its
-// reads of the neighbour vectors after the producers' writes.
-__device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64_t L, int need,
-                                                Header* hdr, int lane,
-                                                unsigned long long wait_ns) {
-  const bool lo = l > 0, up = l < L - 1;
-  if (lane == 0) {
-    unsigned long long t0 = 0;
-    for (int it = 0;; ++it) {
-      const bool ok = (!lo || ld_acquire(ver + l - 1) >= need) &&
-                      (!up || ld_acquire(ver + l + 1) >= need);
-      if (ok) break;
-      if (it == 0) {
-        t0 = global_ns();
-      } else if (global_ns() - t0 > wait_ns) {
-        latch(hdr, MC_ERR_TIMEOUT);
-        break;
-      }
-      __nanosleep(128);
-    }
-  }
-  __syncwarp();
-  if (lo) (void)ld_acquire(ver + l - 1);
-  if (up) (void)ld_acquire(ver + l + 1);
-}
-
-// Level l now holds its version v: every lane's stores of z_l are made
-// visible before the counter.
-__device__ __forceinline__ void publish(int* ver, int v, int lane) {
-  __threadfence();
-  __syncwarp();
-  if (lane == 0) st_release(ver, v);
-}
-
 template <int R, bool COUPLED, bool PAIRED>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
   extern __shared__ double vsh[];
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
   const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
-  unsigned long long q0 = lane == 0 ? atomicAdd(a.claim, 1ull) : 0ull;
+  unsigned long long q0 = claim_unit(a.claim, lane);
   unsigned long long q = __shfl_sync(kFull, q0, 0);
   while (q < total) {
     // claim the next unit now; its index is needed only after this one
-    q0 = lane == 0 ? atomicAdd(a.claim, 1ull) : 0ull;
+    q0 = claim_unit(a.claim, lane);
     const int64_t k = (int64_t)(q / (unsigned long long)a.L);
     const int64_t r = (int64_t)q - k * a.L;
     const bool h2 = r >= a.P0;
@@ -125,22 +74,50 @@ __global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* 
   wait_neighbours(ver, 1, 3, 1, hdr, lane, wait_ns);
 }
 
-// e^T z_K and e^T z_{K-1} from the per-level sums (one block, fixed order).
-__global__ void __launch_bounds__(1024) k_fused_scale(const double* lsum, int64_t L, int64_t K,
-                                                      double* out) {
+// e^T z_K and e^T z_{K-1} from the per-level sums.  FP64 adds run at two
+// lanes per clock per SM here, so the sums are spread over kScaleBlocks
+// blocks, each over a fixed contiguous range of levels; the last block to
+// finish adds the block partials (fixed summation order).
+// part: 2 kScaleBlocks doubles of scratch; ticket: zero between launches.
+__global__ void __launch_bounds__(256) k_fused_scale(const double* lsum, int64_t L, int64_t K,
+                                                     double* part, unsigned* ticket,
+                                                     double* out) {
   __shared__ double sh[32];
+  __shared__ bool last;
   const double* a = lsum + ((K - 1) & 1) * L;
   const double* b = lsum + ((K - 2) & 1) * L;
+  const int64_t chunk = (L + gridDim.x - 1) / gridDim.x;
+  const int64_t l0 = blockIdx.x * chunk;
+  const int64_t l1 = l0 + chunk < L ? l0 + chunk : L;
   double ta = 0.0, tb = 0.0;
-  for (int64_t l = threadIdx.x; l < L; l += blockDim.x) {
+  for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
     ta += a[l];
     if (K >= 2) tb += b[l];
   }
   ta = block_sum(ta, sh);
   tb = block_sum(tb, sh);
   if (threadIdx.x == 0) {
-    out[0] = ta;
-    out[1] = K >= 2 ? tb : 1.0;
+    part[2 * blockIdx.x] = ta;
+    part[2 * blockIdx.x + 1] = tb;
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!last || threadIdx.x >= 32) return;
+  __threadfence();
+  // the first warp loads the partials in parallel (lane i: blocks i, i + 32)
+  // and adds them with a fixed shuffle tree
+  double sa = 0.0, sb = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) {
+    sa += __ldcg(part + 2 * i);
+    sb += __ldcg(part + 2 * i + 1);
+  }
+  sa = warp_sum(sa);
+  sb = warp_sum(sb);
+  if (threadIdx.x == 0) {
+    out[0] = sa;
+    out[1] = K >= 2 ? sb : 1.0;
+    *ticket = 0u;
   }
 }
 
@@ -196,8 +173,8 @@ cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header*
 }
 
 cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
-                               cudaStream_t s) {
-  k_fused_scale<<<1, 1024, 0, s>>>(lsum, L, K, out);
+                               double* part, unsigned* ticket, cudaStream_t s) {
+  k_fused_scale<<<kScaleBlocks, 256, 0, s>>>(lsum, L, K, part, ticket, out);
   return cudaGetLastError();
 }
 

@@ -7,7 +7,8 @@
 //     d_l = (-T_dd)^{-1}(T_lo d_{l-1} + T_up d_{l+1}) + q_l
 //  (inverse mode)  or  W_lo d_{l-1} + W_up d_{l+1} + q_l  (coupled mode),
 // half-sweep 1 on the diagonal-only rows, half-sweep 2 on the coupled rows,
-// in place on one FP32 vector d that starts at zero.
+// in place on one FP32 vector d that starts at zero; all sweeps of a step run
+// as one fused launch.
 // Update (FP64): pi <- (pi + d) / e^T(pi + d).
 //
 // Storage of the streamed blocks: FP32, or BF16 with one power-of-two scale per
@@ -19,7 +20,7 @@
 
 #include "mc_internal.cuh"
 #include "lowprec_dev.cuh"
-#include "sweep_dev.cuh"
+#include "wave_dev.cuh"
 
 namespace mc {
 
@@ -34,26 +35,43 @@ struct LpArgs {
   const float* sc;     // per level: scale of A, scale of B
   float* d;            // iterate, updated in place
   const float* q;      // (-T_dd)^{-1} r
-  int64_t L, P;
-  int m, parity;
+  int64_t L;
+  int m, parity;        // parity: levels of half-sweep 1
   int64_t abs_, cbs;   // block strides in elements (A/B planes, C plane)
 };
 
-// One half-sweep of the correction iteration (one warp per level).
+// All `K` correction sweeps of one refinement step in one persistent launch:
+// units (sweep k, half-sweep h, level l) claimed in order, each waiting for
+// its neighbour levels through per-level completion counters (as the FP64
+// fused sweeps).  d is updated in place; a unit overwrites level l only after
+// the units that read its previous value (its neighbours' previous updates)
+// have completed, which is the condition it waits for.
 template <typename T, int G, int GF, bool COUPLED>
-__global__ void __launch_bounds__(256) k_phase_lp(LpArgs a) {
+__global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver,
+                                                   unsigned long long* claim, Header* hdr,
+                                                   unsigned long long wait_ns) {
   extern __shared__ float fsh[];
   constexpr int SL = LpSlice<T, G, GF>::SL;
   const int lane = threadIdx.x & 31;
   float* slice = fsh + (threadIdx.x >> 5) * 3 * SL;
-  const int nw = (int)((gridDim.x * blockDim.x) >> 5);
-  const int gw = sched_warp(a.P, nw);
   const T* Ap = reinterpret_cast<const T*>(a.A);
   const T* Bp = reinterpret_cast<const T*>(a.B);
-  for (int64_t u = gw; u < a.P; u += nw) {
-    const int64_t l = 2 * u + a.parity;
-    level_sweep_lp<T, G, GF, COUPLED>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_, a.cbs,
-                                      slice, lane);
+  const int64_t P0 = (a.L - a.parity + 1) / 2;   // levels of half-sweep 1
+  const unsigned long long total = (unsigned long long)K * (unsigned long long)a.L;
+  unsigned long long q0 = claim_unit(claim, lane);
+  unsigned long long q = __shfl_sync(0xffffffffu, q0, 0);
+  while (q < total) {
+    q0 = claim_unit(claim, lane);
+    const int64_t k = (int64_t)(q / (unsigned long long)a.L);
+    const int64_t r = (int64_t)q - k * a.L;
+    const bool h2 = r >= P0;
+    const int64_t l = h2 ? 2 * (r - P0) + (1 - a.parity) : 2 * r + a.parity;
+    const int need = (int)(h2 ? k + 1 : k);
+    if (need > 0) wait_neighbours(ver, l, a.L, need, hdr, lane, wait_ns);
+    level_sweep_lp<T, G, GF, COUPLED, true>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_,
+                                            a.cbs, slice, lane);
+    publish(ver + l, (int)(k + 1), lane);
+    q = __shfl_sync(0xffffffffu, q0, 0);
   }
 }
 
@@ -124,31 +142,40 @@ __global__ void __launch_bounds__(256) k_update(const double* __restrict__ pi,
   }
 }
 
+struct LpFused {
+  int64_t K;
+  int* ver;
+  unsigned long long* claim;
+  Header* hdr;
+  unsigned long long wait_ns;
+};
+
 template <typename T, int G, int GF, bool C>
-cudaError_t lp_launch(const LpArgs& a, int nb, cudaStream_t s) {
+cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t s) {
   const size_t smem = (size_t)kWarpsPerBlock * 3 * LpSlice<T, G, GF>::SL * sizeof(float);
   static bool done = false;
   if (!done && smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
-        k_phase_lp<T, G, GF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_sweeps_lp<T, G, GF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     done = true;
   }
-  k_phase_lp<T, G, GF, C><<<nb, 256, smem, s>>>(a);
+  k_sweeps_lp<T, G, GF, C><<<nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr, f.wait_ns);
   return cudaGetLastError();
 }
 
 template <typename T, bool C>
-cudaError_t lp_dispatch(const LpArgs& a, int nb, cudaStream_t s) {
+cudaError_t lp_dispatch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t s) {
   constexpr int V = Pack<T>::V;
   const int G = (a.m + 32 * V - 1) / (32 * V);
   const int GF = (a.m + 63) / 64;
-  if (GF == 1) return lp_launch<T, 1, 1, C>(a, nb, s);
-  if (GF == 2) return G == 1 ? lp_launch<T, 1, 2, C>(a, nb, s) : lp_launch<T, 2, 2, C>(a, nb, s);
+  if (GF == 1) return lp_fused_launch<T, 1, 1, C>(a, f, nb, s);
+  if (GF == 2)
+    return G == 1 ? lp_fused_launch<T, 1, 2, C>(a, f, nb, s) : lp_fused_launch<T, 2, 2, C>(a, f, nb, s);
   if (GF <= 4) {
-    if (G == 1) return lp_launch<T, 1, 4, C>(a, nb, s);
-    if (G == 2) return lp_launch<T, 2, 4, C>(a, nb, s);
-    return lp_launch<T, 4, 4, C>(a, nb, s);
+    if (G == 1) return lp_fused_launch<T, 1, 4, C>(a, f, nb, s);
+    if (G == 2) return lp_fused_launch<T, 2, 4, C>(a, f, nb, s);
+    return lp_fused_launch<T, 4, 4, C>(a, f, nb, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -167,10 +194,11 @@ cudaError_t launch_lp_convert(const double* src, void* dst, int bf16, float* sc,
   return cudaGetLastError();
 }
 
-cudaError_t launch_phase_lp(const void* A, const void* B, const float* C, const float* sc,
-                            float* d, const float* q, int64_t L, int m, int parity,
-                            int64_t abs_, int64_t cbs, int bf16, int coupled, int nb,
-                            cudaStream_t s) {
+cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const float* sc,
+                             float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
+                             int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
+                             unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
+                             int nb, cudaStream_t s) {
   LpArgs a{};
   a.A = A;
   a.B = B;
@@ -179,17 +207,17 @@ cudaError_t launch_phase_lp(const void* A, const void* B, const float* C, const 
   a.d = d;
   a.q = q;
   a.L = L;
-  a.P = (L - parity + 1) / 2;
   a.m = m;
   a.parity = parity;
   a.abs_ = abs_;
   a.cbs = cbs;
+  const LpFused f{K, ver, claim, hdr, wait_ns};
   if (bf16 && m <= 128)
-    return coupled ? lp_dispatch<Bf16x2, true>(a, nb, s) : lp_dispatch<Bf16x2, false>(a, nb, s);
+    return coupled ? lp_dispatch<Bf16x2, true>(a, f, nb, s) : lp_dispatch<Bf16x2, false>(a, f, nb, s);
   if (bf16)
-    return coupled ? lp_dispatch<__nv_bfloat16, true>(a, nb, s)
-                   : lp_dispatch<__nv_bfloat16, false>(a, nb, s);
-  return coupled ? lp_dispatch<float, true>(a, nb, s) : lp_dispatch<float, false>(a, nb, s);
+    return coupled ? lp_dispatch<__nv_bfloat16, true>(a, f, nb, s)
+                   : lp_dispatch<__nv_bfloat16, false>(a, f, nb, s);
+  return coupled ? lp_dispatch<float, true>(a, f, nb, s) : lp_dispatch<float, false>(a, f, nb, s);
 }
 
 cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,

@@ -98,7 +98,8 @@ struct LpSlice {
 //   coupled: d_l = W_lo d_{l-1} + W_up d_{l+1} + q_l,
 // with A/B stored as T (BF16 blocks carry a power-of-two scale sc[2l], sc[2l+1]
 // applied to the input vector) and C = (-T_dd)^{-1} in FP32.
-template <typename T, int G, int GF, bool COUPLED>
+// CG: d is also written by other SMs during the launch (L2 reads).
+template <typename T, int G, int GF, bool COUPLED, bool CG = false>
 __device__ __forceinline__ void level_sweep_lp(const T* A, const T* B, const float* C,
                                                const float* sc, float* d, const float* q,
                                                int64_t l, int64_t L, int m, int64_t abs_,
@@ -110,8 +111,13 @@ __device__ __forceinline__ void level_sweep_lp(const T* A, const T* B, const flo
   const bool has_lo = l > 0, has_up = l < L - 1;
   const float s_lo = sc[2 * l], s_up = sc[2 * l + 1];
   for (int i = lane; i < SL; i += 32) {
-    v_lo[i] = (has_lo && i < m) ? d[(l - 1) * m + i] * s_lo : 0.0f;
-    v_up[i] = (has_up && i < m) ? d[(l + 1) * m + i] * s_up : 0.0f;
+    if constexpr (CG) {
+      v_lo[i] = (has_lo && i < m) ? __ldcg(d + (l - 1) * m + i) * s_lo : 0.0f;
+      v_up[i] = (has_up && i < m) ? __ldcg(d + (l + 1) * m + i) * s_up : 0.0f;
+    } else {
+      v_lo[i] = (has_lo && i < m) ? d[(l - 1) * m + i] * s_lo : 0.0f;
+      v_up[i] = (has_up && i < m) ? d[(l + 1) * m + i] * s_up : 0.0f;
+    }
   }
   __syncwarp();
   float acc[G][V];

@@ -29,7 +29,9 @@ constexpr int kNormThreads = 256;
 
 struct Header {
   int32_t status;        // first device-side error (mc_status), 0 = none
-  uint32_t ticket[7];    // last-block-done counters (0 between launches)
+  uint32_t ticket[7];    // last-block-done counters (0 between launches): [0] normalise,
+                         // [1] residual, [2] half-sweep 2, [3] low-precision update,
+                         // [4] fused scale
   double stats[4];       // [e^T z, step_l1, resid_l1, spare]
 };
 
@@ -162,9 +164,11 @@ cudaError_t launch_sweeps_fused(const FusedArgs& a, int coupled, int n_blocks, c
 // MC_ERR_TIMEOUT is latched in hdr when they never do.
 cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver,
                                  cudaStream_t s);
-// out[0] = e^T z_K, out[1] = e^T z_{K-1} (1 when K = 1), fixed summation order.
+// out[0] = e^T z_K, out[1] = e^T z_{K-1} (1 when K = 1), fixed summation order;
+// part: 2 kScaleBlocks doubles of scratch, ticket: a counter that is zero.
+constexpr int kScaleBlocks = 64;
 cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
-                               cudaStream_t s);
+                               double* part, unsigned* ticket, cudaStream_t s);
 cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
 // Latch MC_ERR_ARG unless the paired zero quadrants of TLO / TUP are zero.
@@ -175,10 +179,13 @@ cudaError_t launch_check_scale(const double* x0, double* x, int64_t n, Header* h
 
 cudaError_t launch_lp_convert(const double* src, void* dst, int bf16, float* sc, int sc_stride,
                               const Layout& lay, int64_t dbs, cudaStream_t s);
-cudaError_t launch_phase_lp(const void* A, const void* B, const float* C, const float* sc,
-                            float* d, const float* q, int64_t L, int m, int parity,
-                            int64_t abs_, int64_t cbs, int bf16, int coupled, int nb,
-                            cudaStream_t s);
+// All K correction sweeps of a refinement step in one launch (ver, claim:
+// zeroed counters as for launch_sweeps_fused; parity of half-sweep 1).
+cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const float* sc,
+                             float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
+                             int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
+                             unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
+                             int nb, cudaStream_t s);
 cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,
                           int nb, Header* hdr, double* s_out, cudaStream_t s);
 

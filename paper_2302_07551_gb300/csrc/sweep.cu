@@ -92,13 +92,20 @@ __global__ void __launch_bounds__(32) k_bgs(PhaseArgs a) {
 
 __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   __shared__ double sh[32];
+  __shared__ double rcp[2];
   __shared__ bool last;
   const double s = *a.s;
   const bool ok = (s > 0.0) && isfinite(s);
   if (!ok && blockIdx.x == 0 && threadIdx.x == 0) latch(a.hdr, MC_ERR_BREAKDOWN);
-  const double inv = 1.0 / s;
   const double so = a.s_old ? *a.s_old : 1.0;
-  const double pinv = 1.0 / so;   // exactly 1 for a normalised x_old
+  // the reciprocals once per block: FP64 division is costly at this FP64 rate
+  if (threadIdx.x == 0) {
+    rcp[0] = 1.0 / s;
+    rcp[1] = 1.0 / so;   // exactly 1 for a normalised x_old
+  }
+  __syncthreads();
+  const double inv = rcp[0];
+  const double pinv = rcp[1];
   double d = 0.0;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool vec = ((((uintptr_t)a.x_old) | ((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0;
@@ -106,17 +113,34 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
       a.x_new[i] = a.z[i] * inv;
   } else if (vec) {
+    // batches of kNormV pairs per thread: all loads of a batch are issued
+    // before its stores (x_new may alias x_old entry by entry)
+    constexpr int kNormV = 4;
     const int64_t n2 = a.N / 2;
     const double2* z2 = reinterpret_cast<const double2*>(a.z);
     const double2* x2 = reinterpret_cast<const double2*>(a.x_old);
     double2* y2 = reinterpret_cast<double2*>(a.x_new);
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
-      const double2 zz = z2[i], xx = x2[i];
-      double2 p;
-      p.x = zz.x * inv;
-      p.y = zz.y * inv;
-      d += fabs(p.x - xx.x * pinv) + fabs(p.y - xx.y * pinv);
-      y2[i] = p;
+    for (int64_t b = (int64_t)blockIdx.x * blockDim.x * kNormV; b < n2; b += stride * kNormV) {
+      double2 zz[kNormV], xx[kNormV];
+#pragma unroll
+      for (int v = 0; v < kNormV; ++v) {
+        const int64_t i = b + v * blockDim.x + threadIdx.x;
+        if (i < n2) {
+          zz[v] = z2[i];
+          xx[v] = x2[i];
+        }
+      }
+#pragma unroll
+      for (int v = 0; v < kNormV; ++v) {
+        const int64_t i = b + v * blockDim.x + threadIdx.x;
+        if (i < n2) {
+          double2 p;
+          p.x = zz[v].x * inv;
+          p.y = zz[v].y * inv;
+          d += fabs(p.x - xx[v].x * pinv) + fabs(p.y - xx[v].y * pinv);
+          y2[i] = p;
+        }
+      }
     }
     if (blockIdx.x == 0 && threadIdx.x == 0 && (a.N & 1)) {
       const int64_t i = a.N - 1;
