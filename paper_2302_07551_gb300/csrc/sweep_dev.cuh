@@ -35,7 +35,7 @@ __device__ __forceinline__ int sched_warp(int64_t P, int nw) {
 template <int R>
 struct Tune {
   static constexpr int U = R <= 1 ? 16 : R <= 2 ? 8 : R <= 4 ? 4 : 2;  // columns per batch
-  static constexpr int NA = 2;                                         // accumulators per row
+  static constexpr int NA = 1;                                         // accumulators per row
   static constexpr int MINB = R <= 4 ? 3 : 2;                          // blocks per SM
 };
 
@@ -152,7 +152,9 @@ __device__ __forceinline__ void zero_acc(double (&acc)[R][Tune<R>::NA]) {
 
 template <int R>
 __device__ __forceinline__ double fold(const double (&a)[Tune<R>::NA]) {
-  if constexpr (Tune<R>::NA == 4) {
+  if constexpr (Tune<R>::NA == 1) {
+    return a[0];
+  } else if constexpr (Tune<R>::NA == 4) {
     return (a[0] + a[1]) + (a[2] + a[3]);
   } else {
     return a[0] + a[1];
