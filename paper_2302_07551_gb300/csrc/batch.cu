@@ -1,5 +1,5 @@
 // Batched kernels of the solve server (see batch.cuh): the per-level bodies
-// of the single-chain kernels (level_sweep, level_resid, level_sweep_lp)
+// of the single-chain kernels (level_sweep2, level_resid, level_sweep_lp)
 // applied to every level of every active request in one persistent launch.
 #include <cuda_bf16.h>
 #include <math.h>
@@ -7,6 +7,7 @@
 #include "batch.cuh"
 #include "lowprec_dev.cuh"
 #include "sweep_dev.cuh"
+#include "wave_dev.cuh"
 
 namespace mc {
 
@@ -36,36 +37,76 @@ __device__ __forceinline__ void bucket(const BTable* t, const int64_t* off, bool
   i1 = off[r1];
 }
 
+constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of one neighbour wait
+
+// Unit q of a fused chunk of K sweeps over one bucket: sweep k, half-sweep h,
+// request r, level l (half-sweep 1 items [a0, a1) of off_h1, then half-sweep 2
+// items [b0, b1) of off_h2).
+struct BUnit {
+  int64_t k, l;
+  int r;
+  bool h2;
+};
+
+__device__ __forceinline__ BUnit unit_of(const BTable* t, unsigned long long q, int64_t n1,
+                                         int64_t U, int64_t a0, int64_t b0, int r0, int r1) {
+  BUnit u;
+  u.k = (int64_t)(q / (unsigned long long)U);
+  const int64_t rr = (int64_t)q - u.k * U;
+  u.h2 = rr >= n1;
+  const int64_t* off = u.h2 ? t->off_h2 : t->off_h1;
+  const int64_t i = u.h2 ? b0 + (rr - n1) : a0 + rr;
+  u.r = find_req(off, r0, r1, i);
+  const int par = u.h2 ? 1 - t->r[u.r].p1 : t->r[u.r].p1;
+  u.l = 2 * (i - off[u.r]) + par;
+  return u;
+}
+
+// K FP64 sweeps of every request of one bucket in one launch.  Per request:
+// sweep 0 reads x, sweeps 0..K-2 write xb in place, sweep K-1 writes z (so xb
+// keeps the previous sweep for the step error).
 template <bool COUPLED, bool LARGE>
-__global__ void __launch_bounds__(256) k_b_phase(const BTable* __restrict__ t, int half) {
+__global__ void __launch_bounds__(256) k_b_sweeps(const BTable* __restrict__ t, int K,
+                                                  unsigned long long* claim, BOut* out) {
   extern __shared__ double vsh[];
   constexpr int RMAX = LARGE ? 8 : 4;
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * RMAX;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t* off = half == 0 ? t->off_h1 : t->off_h2;
   int r0, r1;
-  int64_t i0, i1;
-  bucket(t, off, LARGE, r0, r1, i0, i1);
-  for (int64_t i = i0 + gw; i < i1; i += nw) {
-    const int r = find_req(off, r0, r1, i);
-    const BReq* q = &t->r[r];
-    const int par = half == 0 ? q->p1 : 1 - q->p1;
-    const int64_t l = 2 * (i - off[r]) + par;
-    const double* src = half == 0 ? q->x : q->z;
+  int64_t a0, a1, b0, b1;
+  bucket(t, t->off_h1, LARGE, r0, r1, a0, a1);
+  bucket(t, t->off_h2, LARGE, r0, r1, b0, b1);
+  const int64_t n1 = a1 - a0, U = n1 + (b1 - b0);
+  if (U == 0) return;
+  const unsigned long long total = (unsigned long long)K * (unsigned long long)U;
+  const int base = t->epoch;
+  unsigned long long q0 = claim_unit(claim, lane);
+  unsigned long long q = __shfl_sync(kFull, q0, 0);
+  while (q < total) {
+    q0 = claim_unit(claim, lane);
+    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1);
+    const BReq* Q = &t->r[u.r];
+    const bool last = u.k == K - 1;
+    double* dst = last ? Q->z : Q->xb;
+    const double* src = u.h2 ? dst : (u.k == 0 ? Q->x : Q->xb);
+    if (u.h2 || u.k > 0)
+      wait_neighbours(Q->ver, u.l, Q->L, base + (int)(u.h2 ? u.k + 1 : u.k), &out[u.r].status,
+                      lane, kWaitNs);
     double ls;
     if (LARGE) {
-      ls = level_sweep<8, COUPLED>(q->A, q->B, q->C, src, q->z, l, q->L, q->m, q->ms, slice, lane);
+      ls = level_sweep2<8, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, u.l, Q->L,
+                                                       Q->m, Q->ms, slice, lane);
     } else {
-      switch (q->R) {
-        case 1: ls = level_sweep<1, COUPLED>(q->A, q->B, q->C, src, q->z, l, q->L, q->m, q->ms, slice, lane); break;
-        case 2: ls = level_sweep<2, COUPLED>(q->A, q->B, q->C, src, q->z, l, q->L, q->m, q->ms, slice, lane); break;
-        case 3: ls = level_sweep<3, COUPLED>(q->A, q->B, q->C, src, q->z, l, q->L, q->m, q->ms, slice, lane); break;
-        default: ls = level_sweep<4, COUPLED>(q->A, q->B, q->C, src, q->z, l, q->L, q->m, q->ms, slice, lane); break;
+      switch (Q->R) {
+        case 1: ls = level_sweep2<1, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, u.l, Q->L, Q->m, Q->ms, slice, lane); break;
+        case 2: ls = level_sweep2<2, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, u.l, Q->L, Q->m, Q->ms, slice, lane); break;
+        case 3: ls = level_sweep2<3, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, u.l, Q->L, Q->m, Q->ms, slice, lane); break;
+        default: ls = level_sweep2<4, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, u.l, Q->L, Q->m, Q->ms, slice, lane); break;
       }
     }
-    if (lane == 0) q->lsum[l] = ls;
+    if (lane == 0) Q->lsum2[(u.k & 1) * Q->L + u.l] = ls;
+    publish(Q->ver + u.l, base + (int)u.k + 1, lane);
+    q = __shfl_sync(kFull, q0, 0);
   }
 }
 
@@ -100,14 +141,36 @@ __global__ void __launch_bounds__(256) k_b_resid(const BTable* __restrict__ t, i
   }
 }
 
-// which: 0 -> s = e^T z (with the breakdown check), 1 -> step, 2 -> residual.
+// which: 0 -> s = e^T z (with the breakdown check), 1 -> step, 2 -> residual,
+// 3 -> e^T z of the last two sweeps of a fused chunk of K sweeps (from lsum2).
 // One block per request (grid-stride), fixed order: thread k adds levels
 // k, k + blockDim, ..., then a fixed shuffle tree.
 __global__ void __launch_bounds__(256) k_b_reqsum(const BTable* __restrict__ t, BOut* out,
-                                                  int which) {
+                                                  int which, int K = 1) {
   __shared__ double sh[32];
   for (int r = blockIdx.x; r < t->n; r += gridDim.x) {
     const BReq* q = &t->r[r];
+    if (which == 3) {
+      const double* a = q->lsum2 + ((K - 1) & 1) * q->L;
+      const double* b = q->lsum2 + ((K - 2) & 1) * q->L;
+      double va = 0.0, vb = 0.0;
+      for (int64_t l = threadIdx.x; l < q->L; l += blockDim.x) {
+        va += a[l];
+        if (K >= 2) vb += b[l];
+      }
+      va = block_sum(va, sh);
+      vb = block_sum(vb, sh);
+      if (threadIdx.x == 0) {
+        const double sp = K >= 2 ? vb : 1.0;
+        out[r].s_last = va;
+        out[r].s_prev = sp;
+        out[r].s = va / sp;
+        if (!(va > 0.0) || !isfinite(va) || !(sp > 0.0) || !isfinite(sp))
+          out[r].status = MC_ERR_BREAKDOWN;
+      }
+      __syncthreads();
+      continue;
+    }
     double v = 0.0;
     for (int64_t l = threadIdx.x; l < q->L; l += blockDim.x) v += q->lsum[l];
     v = block_sum(v, sh);
@@ -125,10 +188,13 @@ __global__ void __launch_bounds__(256) k_b_reqsum(const BTable* __restrict__ t, 
   }
 }
 
-// x_l = src_l / s per level (src = z, or xb after a refinement update), with
-// the level's step error |x_new - x_old|_1 into lsum.
+// x_l = src_l / s per level with the level's step error into lsum:
+//   mode 0: src = z, s = e^T z, step against x;
+//   mode 1: src = xb (refinement update), as mode 0;
+//   mode 2: fused chunk of K sweeps: src = z / s_last, step against
+//           x_prev / s_prev with x_prev = xb (K >= 2) or x (K = 1).
 __global__ void __launch_bounds__(256) k_b_norm(const BTable* __restrict__ t, const BOut* out,
-                                                int from_xb) {
+                                                int mode, int K = 1) {
   const int lane = threadIdx.x & 31;
   const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -137,13 +203,15 @@ __global__ void __launch_bounds__(256) k_b_norm(const BTable* __restrict__ t, co
     const int r = find_req(t->off_lv, 0, t->n, i);
     const BReq* q = &t->r[r];
     const int64_t l = i - t->off_lv[r];
-    const double inv = 1.0 / out[r].s;
-    const double* src = from_xb ? q->xb : q->z;
+    const double inv = 1.0 / (mode == 2 ? out[r].s_last : out[r].s);
+    const double pinv = mode == 2 ? 1.0 / out[r].s_prev : 1.0;
+    const double* src = mode == 1 ? q->xb : q->z;
+    const double* prev = (mode == 2 && K >= 2) ? q->xb : q->x;
     double e = 0.0;
     for (int k = lane; k < q->m; k += 32) {
       const int64_t j = l * q->m + k;
       const double p = src[j] * inv;
-      e += fabs(p - q->x[j]);
+      e += fabs(p - prev[j] * pinv);
       q->x[j] = p;
     }
     e = warp_sum(e);
@@ -188,35 +256,48 @@ __global__ void __launch_bounds__(256) k_b_zero_d(const BTable* __restrict__ t) 
 
 // Low-precision size classes: small bucket m <= 64 (G = GF = 1) and
 // m <= 128 (G = GF = 2, FP32 or two-row BF16); large bucket m <= 256
-// (FP32 G = 4, four-row BF16 G = 2; GF = 4).
+// (FP32 G = 4, four-row BF16 G = 2; GF = 4).  All K correction sweeps of a
+// refinement step in one launch per bucket, d in place.
 template <typename TS, typename TL, bool COUPLED, bool LARGE>
-__global__ void __launch_bounds__(256) k_b_phase_lp(const BTable* __restrict__ t, int half) {
+__global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ t, int K,
+                                                     unsigned long long* claim, BOut* out) {
   extern __shared__ float fsh[];
   constexpr int SL = LARGE ? 256 : 128;
   const int lane = threadIdx.x & 31;
   float* slice = fsh + (threadIdx.x >> 5) * 3 * SL;
-  const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int64_t* off = half == 0 ? t->off_h1 : t->off_h2;
   int r0, r1;
-  int64_t i0, i1;
-  bucket(t, off, LARGE, r0, r1, i0, i1);
-  for (int64_t i = i0 + gw; i < i1; i += nw) {
-    const int r = find_req(off, r0, r1, i);
-    const BReq* q = &t->r[r];
-    const int par = half == 0 ? q->p1 : 1 - q->p1;
-    const int64_t l = 2 * (i - off[r]) + par;
+  int64_t a0, a1, b0, b1;
+  bucket(t, t->off_h1, LARGE, r0, r1, a0, a1);
+  bucket(t, t->off_h2, LARGE, r0, r1, b0, b1);
+  const int64_t n1 = a1 - a0, U = n1 + (b1 - b0);
+  if (U == 0) return;
+  const unsigned long long total = (unsigned long long)K * (unsigned long long)U;
+  const int base = t->epoch;
+  unsigned long long q0 = claim_unit(claim, lane);
+  unsigned long long q = __shfl_sync(kFull, q0, 0);
+  while (q < total) {
+    q0 = claim_unit(claim, lane);
+    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1);
+    const BReq* Q = &t->r[u.r];
+    if (u.h2 || u.k > 0)
+      wait_neighbours(Q->ver, u.l, Q->L, base + (int)(u.h2 ? u.k + 1 : u.k), &out[u.r].status,
+                      lane, kWaitNs);
     if (LARGE) {
       constexpr int G = Pack<TL>::V == 2 ? 4 : 2;
-      level_sweep_lp<TL, G, 4, COUPLED>((const TL*)q->lA, (const TL*)q->lB, q->lC, q->sc, q->d,
-                                        q->q, l, q->L, q->m, q->lp_bs, q->lp_cbs, slice, lane);
-    } else if (q->m <= 64) {
-      level_sweep_lp<TS, 1, 1, COUPLED>((const TS*)q->lA, (const TS*)q->lB, q->lC, q->sc, q->d,
-                                        q->q, l, q->L, q->m, q->lp_bs, q->lp_cbs, slice, lane);
+      level_sweep_lp<TL, G, 4, COUPLED, true>((const TL*)Q->lA, (const TL*)Q->lB, Q->lC, Q->sc,
+                                              Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
+                                              slice, lane);
+    } else if (Q->m <= 64) {
+      level_sweep_lp<TS, 1, 1, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
+                                              Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
+                                              slice, lane);
     } else {
-      level_sweep_lp<TS, 2, 2, COUPLED>((const TS*)q->lA, (const TS*)q->lB, q->lC, q->sc, q->d,
-                                        q->q, l, q->L, q->m, q->lp_bs, q->lp_cbs, slice, lane);
+      level_sweep_lp<TS, 2, 2, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
+                                              Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
+                                              slice, lane);
     }
+    publish(Q->ver + u.l, base + (int)u.k + 1, lane);
+    q = __shfl_sync(kFull, q0, 0);
   }
 }
 
@@ -227,36 +308,38 @@ cudaError_t allow(K kernel, size_t bytes) {
 }
 
 template <bool C>
-cudaError_t phase_pair(const BTable* t, int half, BGrid g, cudaStream_t s) {
+cudaError_t sweeps_pair(const BTable* t, unsigned long long* claim, BOut* out, int K, BGrid g,
+                        cudaStream_t s) {
   const size_t sm_small = (size_t)(g.threads / 32) * 3 * 32 * 4 * sizeof(double);
   const size_t sm_large = (size_t)(g.threads / 32) * 3 * 32 * 8 * sizeof(double);
-  cudaError_t e = allow(k_b_phase<C, true>, sm_large);
+  cudaError_t e = allow(k_b_sweeps<C, true>, sm_large);
   if (e != cudaSuccess) return e;
-  k_b_phase<C, false><<<g.blocks, g.threads, sm_small, s>>>(t, half);
-  k_b_phase<C, true><<<g.blocks, g.threads, sm_large, s>>>(t, half);
+  k_b_sweeps<C, false><<<g.blocks, g.threads, sm_small, s>>>(t, K, claim, out);
+  k_b_sweeps<C, true><<<g.blocks, g.threads, sm_large, s>>>(t, K, claim + 1, out);
   return cudaGetLastError();
 }
 
 template <typename TS, typename TL, bool C>
-cudaError_t lp_pair(const BTable* t, int half, BGrid g, cudaStream_t s) {
+cudaError_t lp_pair(const BTable* t, unsigned long long* claim, BOut* out, int K, BGrid g,
+                    cudaStream_t s) {
   const size_t sm_small = (size_t)(g.threads / 32) * 3 * 128 * sizeof(float);
   const size_t sm_large = (size_t)(g.threads / 32) * 3 * 256 * sizeof(float);
-  cudaError_t e = allow(k_b_phase_lp<TS, TL, C, true>, sm_large);
+  cudaError_t e = allow(k_b_sweeps_lp<TS, TL, C, true>, sm_large);
   if (e != cudaSuccess) return e;
-  k_b_phase_lp<TS, TL, C, false><<<g.blocks, g.threads, sm_small, s>>>(t, half);
-  k_b_phase_lp<TS, TL, C, true><<<g.blocks, g.threads, sm_large, s>>>(t, half);
+  k_b_sweeps_lp<TS, TL, C, false><<<g.blocks, g.threads, sm_small, s>>>(t, K, claim, out);
+  k_b_sweeps_lp<TS, TL, C, true><<<g.blocks, g.threads, sm_large, s>>>(t, K, claim + 1, out);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t b_sweep(const BTable* t, BOut* out, int coupled, BGrid g, cudaStream_t s) {
-  for (int half = 0; half < 2; ++half) {
-    const cudaError_t e = coupled ? phase_pair<true>(t, half, g, s) : phase_pair<false>(t, half, g, s);
-    if (e != cudaSuccess) return e;
-  }
-  k_b_reqsum<<<g.blocks, 256, 0, s>>>(t, out, 0);
-  k_b_norm<<<g.blocks, g.threads, 0, s>>>(t, out, 0);
+cudaError_t b_sweeps(const BTable* t, unsigned long long* t_claim, BOut* out, int coupled, int K,
+                     BGrid g, cudaStream_t s) {
+  const cudaError_t e = coupled ? sweeps_pair<true>(t, t_claim, out, K, g, s)
+                                : sweeps_pair<false>(t, t_claim, out, K, g, s);
+  if (e != cudaSuccess) return e;
+  k_b_reqsum<<<g.blocks, 256, 0, s>>>(t, out, 3, K);
+  k_b_norm<<<g.blocks, g.threads, 0, s>>>(t, out, 2, K);
   k_b_reqsum<<<g.blocks, 256, 0, s>>>(t, out, 1);
   return cudaGetLastError();
 }
@@ -272,20 +355,17 @@ cudaError_t b_resid(const BTable* t, BOut* out, int with_q, BGrid g, cudaStream_
   return cudaGetLastError();
 }
 
-cudaError_t b_lp_step(const BTable* t, BOut* out, int bf16, int coupled, int inner, BGrid g,
-                      cudaStream_t s) {
+cudaError_t b_lp_step(const BTable* t, unsigned long long* t_claim, BOut* out, int bf16,
+                      int coupled, int inner, BGrid g, cudaStream_t s) {
   k_b_zero_d<<<g.blocks, g.threads, 0, s>>>(t);
-  for (int k = 0; k < inner; ++k)
-    for (int half = 0; half < 2; ++half) {
-      cudaError_t e;
-      if (bf16)
-        e = coupled ? lp_pair<Bf16x2, __nv_bfloat16, true>(t, half, g, s)
-                    : lp_pair<Bf16x2, __nv_bfloat16, false>(t, half, g, s);
-      else
-        e = coupled ? lp_pair<float, float, true>(t, half, g, s)
-                    : lp_pair<float, float, false>(t, half, g, s);
-      if (e != cudaSuccess) return e;
-    }
+  cudaError_t e;
+  if (bf16)
+    e = coupled ? lp_pair<Bf16x2, __nv_bfloat16, true>(t, t_claim, out, inner, g, s)
+                : lp_pair<Bf16x2, __nv_bfloat16, false>(t, t_claim, out, inner, g, s);
+  else
+    e = coupled ? lp_pair<float, float, true>(t, t_claim, out, inner, g, s)
+                : lp_pair<float, float, false>(t, t_claim, out, inner, g, s);
+  if (e != cudaSuccess) return e;
   k_b_update<<<g.blocks, g.threads, 0, s>>>(t);
   k_b_reqsum<<<g.blocks, 256, 0, s>>>(t, out, 0);
   k_b_norm<<<g.blocks, g.threads, 0, s>>>(t, out, 1);

@@ -11,6 +11,14 @@
 // Every reduction is per level first (one partial per level), then per
 // request in level order: a request's iterates do not depend on which other
 // requests share the launch, nor on the grid shape the autotuner picks.
+//
+// The sweeps of a chunk run fused (as the single-chain fused sweeps): one
+// persistent launch per bucket for all sweeps of the chunk, units claimed in
+// order, each waiting for its neighbour levels through the request's
+// completion counters.  Counters grow across chunks: a chunk with epoch E
+// writes E + k + 1 after its sweep k, so counters never need resetting (new
+// requests start at zero <= E); the two claim counters live in the table and
+// are reset by the table copy that starts every chunk.
 #pragma once
 #include "mc_internal.cuh"
 
@@ -36,6 +44,8 @@ struct BReq {
   double* z;            // unnormalised sweep output
   double* xb;           // pi + d before renormalisation
   double* lsum;         // one partial per level
+  double* lsum2;        // fused sweeps: [2][L] level sums of the last two sweeps
+  int* ver;             // fused sweeps: per-level completion counters
   int64_t L;
   int32_t m, ms, R, p1;  // p1: 0-based parity of the diagonal-only rows
   int64_t lp_bs, lp_cbs;
@@ -44,7 +54,9 @@ struct BReq {
 struct BTable {
   int32_t n;            // active requests
   int32_t n_small;      // requests [0, n_small) have m <= 128
-  int32_t pad[2];
+  int32_t epoch;        // completion-counter base of this chunk
+  int32_t pad;
+  unsigned long long claim[2];   // queue counters of the small / large bucket (0 in t_host)
   int64_t off_h1[kMaxReq + 1];   // prefix counts of half-sweep-1 levels
   int64_t off_h2[kMaxReq + 1];   // prefix counts of half-sweep-2 levels
   int64_t off_lv[kMaxReq + 1];   // prefix counts of all levels
@@ -53,6 +65,7 @@ struct BTable {
 
 struct BOut {
   double s, step, resid;
+  double s_last, s_prev;   // fused FP64 chunk: e^T z of its last two sweeps (s_prev = 1 for one)
   int32_t status;
   int32_t pad;
 };
@@ -61,13 +74,15 @@ struct BGrid {
   int blocks, threads;
 };
 
-// One FP64 sweep of every request: both half-sweeps, e^T z, normalisation and
-// step error.  coupled: server-wide apply mode.
-cudaError_t b_sweep(const BTable* t, BOut* out, int coupled, BGrid g, cudaStream_t s);
+// K FP64 sweeps of every request (fused, no normalisation in between), then
+// e^T z, normalisation and the step error of the last sweep.  t_claim: the
+// device table's claim counters.  coupled: server-wide apply mode.
+cudaError_t b_sweeps(const BTable* t, unsigned long long* t_claim, BOut* out, int coupled, int K,
+                     BGrid g, cudaStream_t s);
 // Direct residual of every request's iterate (with_q: also q for refinement).
 cudaError_t b_resid(const BTable* t, BOut* out, int with_q, BGrid g, cudaStream_t s);
 // Mixed precision: d = 0; `inner` correction sweeps; pi <- (pi + d)/e^T(pi + d).
-cudaError_t b_lp_step(const BTable* t, BOut* out, int bf16, int coupled, int inner, BGrid g,
-                      cudaStream_t s);
+cudaError_t b_lp_step(const BTable* t, unsigned long long* t_claim, BOut* out, int bf16,
+                      int coupled, int inner, BGrid g, cudaStream_t s);
 
 }  // namespace mc

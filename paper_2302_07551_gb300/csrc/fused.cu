@@ -56,7 +56,7 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
     // half-sweep 1 reads z_k (x_in for k = 0); half-sweep 2 reads z_{k+1}
     const double* src = h2 ? dst : (k == 0 ? a.x_in : a.W);
     const int need = (int)(h2 ? k + 1 : k);
-    if (need > 0) wait_neighbours(a.ver, l, a.L, need, a.hdr, lane, a.wait_ns);
+    if (need > 0) wait_neighbours(a.ver, l, a.L, need, &a.hdr->status, lane, a.wait_ns);
     const double t = level_sweep2<R, COUPLED, PAIRED, true, true>(
         a.A, a.B, a.C, src, src, dst, l, a.L, a.m, a.ms, slice, lane);
     if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
@@ -71,7 +71,7 @@ __global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* 
   const int lane = threadIdx.x & 31;
   if (lane < 3) ver[lane] = preset;
   __syncwarp();
-  wait_neighbours(ver, 1, 3, 1, hdr, lane, wait_ns);
+  wait_neighbours(ver, 1, 3, 1, &hdr->status, lane, wait_ns);
 }
 
 // e^T z_K and e^T z_{K-1} from the per-level sums.  FP64 adds run at two

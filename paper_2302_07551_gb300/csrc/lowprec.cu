@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver
     const bool h2 = r >= P0;
     const int64_t l = h2 ? 2 * (r - P0) + (1 - a.parity) : 2 * r + a.parity;
     const int need = (int)(h2 ? k + 1 : k);
-    if (need > 0) wait_neighbours(ver, l, a.L, need, hdr, lane, wait_ns);
+    if (need > 0) wait_neighbours(ver, l, a.L, need, &hdr->status, lane, wait_ns);
     level_sweep_lp<T, G, GF, COUPLED, true>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_,
                                             a.cbs, slice, lane);
     publish(ver + l, (int)(k + 1), lane);

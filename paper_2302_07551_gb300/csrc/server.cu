@@ -3,8 +3,8 @@
 // Requests (independent chains of any L and m <= 256) are admitted into a
 // caller-owned device arena as long as their workspace fits; each step runs
 // one chunk of check_every sweeps for ALL active requests with the batched
-// kernels of batch.cu (one persistent launch per half-sweep and block-size
-// bucket), then reads every request's residual and retires the converged
+// kernels of batch.cu (one fused persistent launch per block-size bucket for
+// all sweeps of the chunk), then reads every request's residual and retires the converged
 // ones.  New requests join at the next chunk, so their work overlaps with the
 // requests already running.  A chunk is one CUDA graph, captured once per
 // (grid, chunk length) and replayed: the kernels read the request table from
@@ -69,6 +69,7 @@ struct mc_server {
   int g_chunk;
   std::map<uint64_t, BGrid> tuned;
   int64_t chunks;
+  int32_t epoch_next;   // completion-counter base of the next chunk
 };
 
 namespace {
@@ -146,6 +147,8 @@ void fill_req(const mc_server* s, const Req* r, BReq* q) {
   q->z = c->z;
   q->xb = c->xb;
   q->lsum = r->lsum;
+  q->lsum2 = c->flsum;
+  q->ver = c->fver;
   q->L = c->lay.L;
   q->m = c->lay.m;
   q->ms = c->lay.ms;
@@ -180,8 +183,16 @@ int retire(mc_server* s, size_t i, int status, double resid, double step, double
   return rc;
 }
 
-// Chunk body on stream st: c sweeps (FP64) or one refinement step of c
-// correction sweeps (low precision), then every request's residual.
+// The next chunk (about to run) uses the current counter base; the one after
+// it starts c higher.  Called before each execution of a chunk (a direct
+// enqueue or a graph launch), while no chunk is in flight.
+void begin_chunk(mc_server* s, int c) {
+  s->t_host->epoch = s->epoch_next;
+  s->epoch_next += c;
+}
+
+// Chunk body on stream st: c fused sweeps (FP64) or one refinement step of c
+// fused correction sweeps (low precision), then every request's residual.
 int enqueue_chunk(mc_server* s, BGrid g, int c, cudaStream_t st) {
   const bool lp = s->d.dtype != MC_F64;
   const int coupled = s->d.apply == MC_APPLY_COUPLED;
@@ -189,12 +200,14 @@ int enqueue_chunk(mc_server* s, BGrid g, int c, cudaStream_t st) {
           cudaSuccess ||
       cudaMemsetAsync(s->out_dev, 0, sizeof(BOut) * kMaxReq, st) != cudaSuccess)
     return MC_ERR_CUDA;
+  unsigned long long* claim = &s->t_dev->claim[0];
   if (lp) {
-    if (b_lp_step(s->t_dev, s->out_dev, s->d.dtype == MC_BF16, coupled, c, g, st) != cudaSuccess)
+    if (b_lp_step(s->t_dev, claim, s->out_dev, s->d.dtype == MC_BF16, coupled, c, g, st) !=
+        cudaSuccess)
       return MC_ERR_CUDA;
   } else {
-    for (int k = 0; k < c; ++k)
-      if (b_sweep(s->t_dev, s->out_dev, coupled, g, st) != cudaSuccess) return MC_ERR_CUDA;
+    if (b_sweeps(s->t_dev, claim, s->out_dev, coupled, c, g, st) != cudaSuccess)
+      return MC_ERR_CUDA;
   }
   if (b_resid(s->t_dev, s->out_dev, lp ? 1 : 0, g, st) != cudaSuccess) return MC_ERR_CUDA;
   if (cudaMemcpyAsync(s->out_host, s->out_dev, sizeof(BOut) * kMaxReq, cudaMemcpyDeviceToHost,
@@ -374,6 +387,9 @@ int mc_server_submit(mc_server* s, int64_t tag, int64_t L, int32_t m, const doub
       cudaMemcpy2DAsync(P + kPlaneTDD * pe, dp, loc, sp, sp, (size_t)L, cudaMemcpyHostToDevice,
                         s->user) != cudaSuccess)
     rc = MC_ERR_CUDA;
+  if (rc == MC_OK &&
+      cudaMemsetAsync(c->fver, 0, (size_t)L * sizeof(int), s->user) != cudaSuccess)
+    rc = MC_ERR_CUDA;
   if (rc == MC_OK) rc = chain_factor_async(c);
   if (rc == MC_OK && launch_fill(c->xa, y.N, 1.0 / (double)y.N, s->user) != cudaSuccess)
     rc = MC_ERR_CUDA;
@@ -422,7 +438,10 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
       for (int k = 1; k <= 4 && rc == MC_OK; ++k) {
         const BGrid gk{k * s->num_sms, 256};
         if (cudaEventRecord(e0, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
-        if (rc == MC_OK) rc = enqueue_chunk(s, gk, c, s->user);
+        if (rc == MC_OK) {
+          begin_chunk(s, c);
+          rc = enqueue_chunk(s, gk, c, s->user);
+        }
         if (rc == MC_OK && cudaEventRecord(e1, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
         if (rc == MC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = MC_ERR_CUDA;
         float ms = 0.0f;
@@ -465,6 +484,7 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
         s->g_chunk = c;
         s->g_grid = g;
       }
+      begin_chunk(s, c);
       if (cudaGraphLaunch(s->gexec, s->user) != cudaSuccess ||
           cudaStreamSynchronize(s->user) != cudaSuccess)
         return MC_ERR_CUDA;

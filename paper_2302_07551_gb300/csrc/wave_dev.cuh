@@ -32,11 +32,12 @@ __device__ __forceinline__ unsigned long long global_ns() {
 }
 
 // Wait until levels l-1 and l+1 (where they exist) have completed `need`
-// writes in this launch, for at most wait_ns nanoseconds.  Lane 0 polls; then
+// writes, for at most wait_ns nanoseconds (then MC_ERR_TIMEOUT is latched in
+// *status unless it holds an earlier error).  Lane 0 polls; then
 // every lane performs its own acquire of both counters, which orders its
 // reads of the neighbour vectors after the producers' writes.
 __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64_t L, int need,
-                                                Header* hdr, int lane,
+                                                int* status, int lane,
                                                 unsigned long long wait_ns) {
   const bool lo = l > 0, up = l < L - 1;
   if (lane == 0) {
@@ -48,7 +49,7 @@ __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64
       if (it == 0) {
         t0 = global_ns();
       } else if (global_ns() - t0 > wait_ns) {
-        latch(hdr, MC_ERR_TIMEOUT);
+        atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
         break;
       }
       __nanosleep(128);
