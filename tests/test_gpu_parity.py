@@ -240,6 +240,40 @@ def test_full_size_qbd_L32768_m64_sampled():
     ch.close()
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("name", ["qbd_L16384_m256", "penta_L8192_m128"])
+def test_full_size_sampled_other_workloads(name):
+    """The other FP64 bench workloads at full size, in the bench's launch
+    configuration (fused sweeps; the pentadiagonal chain paired into 4096
+    super-levels of 256 with the zero quadrants skipped): GPU sweep k+1
+    against the oracle's sweep of the GPU iterate k on sampled windows."""
+    L, m = synth.workload_shape(name)
+    paired = synth.WORKLOADS[name]["kind"] == "penta"
+    blocks = synth.workload(name)
+    ch = mc.Chain(*(dev(b) for b in blocks), paired=paired)
+    del blocks
+    N = L * m
+    x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    xk = ch.sweep(x, nsweeps=4)
+    stats = torch.zeros(3, dtype=torch.float64, device="cuda")
+    xk1 = ch.sweep(xk, nsweeps=1, stats=stats)
+    s = float(stats[0])
+    xk = xk.cpu().numpy()
+    xk1 = xk1.cpu().numpy()
+    for a in (0, 2, L // 2, L - 24):     # even starts: the window keeps the global parity
+        b = min(a + 24, L)
+        sub = oracle.Chain(*synth.workload(name, a, b))
+        z = sub.sweep(xk[a * m:b * m])
+        lo = a if a == 0 else a + 2
+        hi = b if b == L else b - 2
+        got = xk1[lo * m:hi * m]
+        ref = z[(lo - a) * m:(hi - a) * m] / s
+        assert rel_l1(got, ref) <= 1e-12, (name, a)
+    assert abs(xk1.sum() - 1) <= 1e-12 and (xk1 >= 0).all()
+    ch.sync()
+    ch.close()
+
+
 # --- paired block-pentadiagonal chains: zero quadrants skipped ------------------------
 
 @pytest.mark.parametrize("Lp,mp", [(12, 32), (10, 64), (8, 128), (9, 96)])
