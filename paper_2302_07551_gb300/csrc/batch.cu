@@ -4,6 +4,8 @@
 #include <cuda_bf16.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "batch.cuh"
 #include "lowprec_dev.cuh"
 #include "sweep_dev.cuh"
@@ -287,6 +289,22 @@ __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ 
       level_sweep_lp<TL, G, 4, COUPLED, true>((const TL*)Q->lA, (const TL*)Q->lB, Q->lC, Q->sc,
                                               Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
                                               slice, lane);
+    } else if (Q->m <= 64 && (sizeof(TS) == 4 || Q->m % 8 == 0)) {
+      // 16-byte lane loads (BF16 columns 16-byte aligned when m % 8 == 0)
+      using S = typename std::conditional<sizeof(TS) == 4 && !std::is_same<TS, Bf16x2>::value,
+                                          float, unsigned short>::type;
+      if (Q->m <= 16)
+        level_sweep_lp_small<S, 16, COUPLED, true>((const S*)Q->lA, (const S*)Q->lB, Q->lC, Q->sc,
+                                                   Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs,
+                                                   Q->lp_cbs, slice, lane);
+      else if (Q->m <= 32)
+        level_sweep_lp_small<S, 32, COUPLED, true>((const S*)Q->lA, (const S*)Q->lB, Q->lC, Q->sc,
+                                                   Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs,
+                                                   Q->lp_cbs, slice, lane);
+      else
+        level_sweep_lp_small<S, 64, COUPLED, true>((const S*)Q->lA, (const S*)Q->lB, Q->lC, Q->sc,
+                                                   Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs,
+                                                   Q->lp_cbs, slice, lane);
     } else if (Q->m <= 64) {
       level_sweep_lp<TS, 1, 1, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
                                               Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,

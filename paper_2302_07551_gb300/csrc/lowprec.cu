@@ -46,7 +46,18 @@ struct LpArgs {
 // fused sweeps).  d is updated in place; a unit overwrites level l only after
 // the units that read its previous value (its neighbours' previous updates)
 // have completed, which is the condition it waits for.
-template <typename T, int G, int GF, bool COUPLED>
+template <typename T>
+struct SmallOf {
+  using type = unsigned short;   // BF16 bits
+};
+template <>
+struct SmallOf<float> {
+  using type = float;
+};
+
+// SMALL = 16, 32 or 64: blocks of at most SMALL rows through
+// level_sweep_lp_small; 0: level_sweep_lp.
+template <typename T, int G, int GF, bool COUPLED, int SMALL = 0>
 __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver,
                                                    unsigned long long* claim, Header* hdr,
                                                    unsigned long long wait_ns) {
@@ -68,8 +79,16 @@ __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver
     const int64_t l = h2 ? 2 * (r - P0) + (1 - a.parity) : 2 * r + a.parity;
     const int need = (int)(h2 ? k + 1 : k);
     if (need > 0) wait_neighbours(ver, l, a.L, need, &hdr->status, lane, wait_ns);
-    level_sweep_lp<T, G, GF, COUPLED, true>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_,
-                                            a.cbs, slice, lane);
+    if constexpr (SMALL > 0) {
+      using S = typename SmallOf<T>::type;
+      level_sweep_lp_small<S, SMALL, COUPLED, true>(reinterpret_cast<const S*>(a.A),
+                                                    reinterpret_cast<const S*>(a.B), a.C, a.sc,
+                                                    a.d, a.q, l, a.L, a.m, a.abs_, a.cbs, slice,
+                                                    lane);
+    } else {
+      level_sweep_lp<T, G, GF, COUPLED, true>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_,
+                                              a.cbs, slice, lane);
+    }
     publish(ver + l, (int)(k + 1), lane);
     q = __shfl_sync(0xffffffffu, q0, 0);
   }
@@ -150,17 +169,17 @@ struct LpFused {
   unsigned long long wait_ns;
 };
 
-template <typename T, int G, int GF, bool C>
+template <typename T, int G, int GF, bool C, int SMALL = 0>
 cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t s) {
   const size_t smem = (size_t)kWarpsPerBlock * 3 * LpSlice<T, G, GF>::SL * sizeof(float);
   static bool done = false;
   if (!done && smem > 40 * 1024) {
     const cudaError_t e = cudaFuncSetAttribute(
-        k_sweeps_lp<T, G, GF, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_sweeps_lp<T, G, GF, C, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     done = true;
   }
-  k_sweeps_lp<T, G, GF, C><<<nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr, f.wait_ns);
+  k_sweeps_lp<T, G, GF, C, SMALL><<<nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr, f.wait_ns);
   return cudaGetLastError();
 }
 
@@ -169,6 +188,12 @@ cudaError_t lp_dispatch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t 
   constexpr int V = Pack<T>::V;
   const int G = (a.m + 32 * V - 1) / (32 * V);
   const int GF = (a.m + 63) / 64;
+  // at most 64 rows: 16-byte lane loads (BF16 columns must be 16-byte aligned)
+  if (GF == 1 && (sizeof(typename SmallOf<T>::type) == 4 || a.m % 8 == 0)) {
+    if (a.m <= 16) return lp_fused_launch<T, 1, 1, C, 16>(a, f, nb, s);
+    if (a.m <= 32) return lp_fused_launch<T, 1, 1, C, 32>(a, f, nb, s);
+    return lp_fused_launch<T, 1, 1, C, 64>(a, f, nb, s);
+  }
   if (GF == 1) return lp_fused_launch<T, 1, 1, C>(a, f, nb, s);
   if (GF == 2)
     return G == 1 ? lp_fused_launch<T, 1, 2, C>(a, f, nb, s) : lp_fused_launch<T, 2, 2, C>(a, f, nb, s);

@@ -162,5 +162,116 @@ __device__ __forceinline__ void level_sweep_lp(const T* A, const T* B, const flo
   __syncwarp();
 }
 
+// ---- blocks of at most ROWS = 16, 32 or 64 rows: 16-byte lane loads -------
+// S = float (E = 4 rows per load) or unsigned short (BF16 bits, E = 8; needs
+// m % 8 == 0 so that every column starts on a 16-byte boundary).  LPC = ROWS /
+// E lanes cover one column (rows E (lane % LPC) ..), CPW = 32 / LPC columns
+// per warp load, B loads in flight per lane (at most 64 columns per batch, so
+// v is read inside its 64-float slice); lanes of one row group hold partial
+// sums over different columns until small_combine adds them.
+template <typename S, int ROWS>
+struct SmallLp {
+  static constexpr int E = 16 / (int)sizeof(S), LPC = ROWS / E, CPW = 32 / LPC;
+  static constexpr int B = 64 / CPW < 8 ? 64 / CPW : 8;
+};
+
+__device__ __forceinline__ float small_elem(const uint4& t, int e, float) {
+  return __uint_as_float(e == 0 ? t.x : e == 1 ? t.y : e == 2 ? t.z : t.w);
+}
+__device__ __forceinline__ float small_elem(const uint4& t, int e, unsigned short) {
+  const unsigned w = (e >> 1) == 0 ? t.x : (e >> 1) == 1 ? t.y : (e >> 1) == 2 ? t.z : t.w;
+  return __uint_as_float((e & 1) ? (w & 0xffff0000u) : (w << 16));
+}
+
+// acc[e] += sum over this lane's columns j of M(r0 + e, j) v[j]; v: slice of at
+// least 64 floats, zero beyond m.
+template <typename S, int ROWS>
+__device__ __forceinline__ void gemv_small(float (&acc)[SmallLp<S, ROWS>::E],
+                                           const S* __restrict__ M, const float* v, int m,
+                                           int lane) {
+  using P = SmallLp<S, ROWS>;
+  const int c = lane / P::LPC, r0 = P::E * (lane % P::LPC);
+  const bool rok = r0 < m;
+  for (int jb = 0; jb < m; jb += P::CPW * P::B) {
+    uint4 t[P::B];
+#pragma unroll
+    for (int b = 0; b < P::B; ++b) {
+      const int j = jb + b * P::CPW + c;
+      t[b] = (rok && j < m) ? __ldcs(reinterpret_cast<const uint4*>(M + (size_t)j * m + r0))
+                            : make_uint4(0u, 0u, 0u, 0u);
+    }
+#pragma unroll
+    for (int b = 0; b < P::B; ++b) {
+      const float vj = v[jb + b * P::CPW + c];
+#pragma unroll
+      for (int e = 0; e < P::E; ++e) acc[e] = fmaf(small_elem(t[b], e, S()), vj, acc[e]);
+    }
+  }
+}
+
+// Add the CPW partial sums of each row group (fixed shuffle tree); every lane
+// ends with the totals of rows r0 ..
+template <typename S, int ROWS>
+__device__ __forceinline__ void small_combine(float (&acc)[SmallLp<S, ROWS>::E]) {
+  using P = SmallLp<S, ROWS>;
+#pragma unroll
+  for (int o = P::LPC; o < 32; o <<= 1)
+#pragma unroll
+    for (int e = 0; e < P::E; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
+}
+
+// level_sweep_lp for m <= ROWS <= 64 (S as gemv_small; C is FP32).
+template <typename S, int ROWS, bool COUPLED, bool CG = false>
+__device__ __forceinline__ void level_sweep_lp_small(const S* A, const S* B, const float* C,
+                                                     const float* sc, float* d, const float* q,
+                                                     int64_t l, int64_t L, int m, int64_t abs_,
+                                                     int64_t cbs, float* slice, int lane) {
+  constexpr int SL = 64, E = SmallLp<S, ROWS>::E, LPC = SmallLp<S, ROWS>::LPC;
+  float* v_lo = slice;
+  float* v_up = slice + SL;
+  float* v_g = slice + 2 * SL;
+  const bool has_lo = l > 0, has_up = l < L - 1;
+  const float s_lo = sc[2 * l], s_up = sc[2 * l + 1];
+  for (int i = lane; i < SL; i += 32) {
+    if constexpr (CG) {
+      v_lo[i] = (has_lo && i < m) ? __ldcg(d + (l - 1) * m + i) * s_lo : 0.0f;
+      v_up[i] = (has_up && i < m) ? __ldcg(d + (l + 1) * m + i) * s_up : 0.0f;
+    } else {
+      v_lo[i] = (has_lo && i < m) ? d[(l - 1) * m + i] * s_lo : 0.0f;
+      v_up[i] = (has_up && i < m) ? d[(l + 1) * m + i] * s_up : 0.0f;
+    }
+  }
+  __syncwarp();
+  float acc[E];
+#pragma unroll
+  for (int e = 0; e < E; ++e) acc[e] = 0.0f;
+  if (has_lo) gemv_small<S, ROWS>(acc, A + l * abs_, v_lo, m, lane);
+  if (has_up) gemv_small<S, ROWS>(acc, B + l * abs_, v_up, m, lane);
+  small_combine<S, ROWS>(acc);
+  const int r0 = E * (lane % LPC);
+  const bool writer = lane < LPC && r0 < m;   // one lane per row group
+  if (COUPLED) {
+    if (writer)
+#pragma unroll
+      for (int e = 0; e < E; ++e) d[l * m + r0 + e] = acc[e] + q[l * m + r0 + e];
+  } else {
+    for (int i = lane; i < SL; i += 32) v_g[i] = 0.0f;
+    __syncwarp();
+    if (writer)
+#pragma unroll
+      for (int e = 0; e < E; ++e) v_g[r0 + e] = acc[e];
+    __syncwarp();
+    constexpr int LPC2 = SmallLp<float, ROWS>::LPC;
+    float acc2[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    gemv_small<float, ROWS>(acc2, C + l * cbs, v_g, m, lane);
+    small_combine<float, ROWS>(acc2);
+    const int r2 = 4 * (lane % LPC2);
+    if (lane < LPC2 && r2 < m)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) d[l * m + r2 + e] = acc2[e] + q[l * m + r2 + e];
+  }
+  __syncwarp();
+}
+
 }  // namespace dev
 }  // namespace mc

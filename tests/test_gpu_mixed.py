@@ -32,7 +32,8 @@ def rel_l1(a, b):
 @pytest.mark.parametrize("dtype,tol", [("f32", 2e-6), ("bf16", 2e-2)])
 @pytest.mark.parametrize("apply", ["inverse", "coupled"])
 @pytest.mark.parametrize("L,m,stair", [(40, 64, 1), (13, 256, 1), (9, 128, 2), (30, 12, 1),
-                                        (7, 132, 1), (11, 200, 2)])
+                                        (7, 132, 1), (11, 200, 2), (21, 40, 2), (17, 36, 1),
+                                        (5, 8, 1), (19, 16, 1), (10, 32, 2), (12, 20, 1)])
 def test_one_refinement_step(L, m, stair, apply, dtype, tol):
     K = 12
     blocks = synth.qbd(L, m, 0.85, seed=L + m)
