@@ -341,13 +341,17 @@ def run_mine(args):
     if ws == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-    kname = "k_sweeps" if fused else "k_phase"
+    if args.dtype == "f64":
+        kname = "k_sweeps" if fused else "k_phase"
+        key = f"{name}:{args.apply}"
+    else:
+        kname = "k_sweeps_lp"
+        key = f"{name}:{args.apply}:{args.dtype}"
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if args.dtype == "f64" and os.path.exists(tp):
+    if os.path.exists(tp):
         with open(tp) as f:
             tk = json.load(f).get("kernels", {}).get(kname)
-        key = f"{name}:{args.apply}"
         # counters taken on an older kernel source do not describe this one
         if tk and key in tk["workloads"] and tk["kernel_src_sha256"] == src_hash(tk["sources"]):
             w = tk["workloads"][key]
@@ -363,7 +367,7 @@ def run_mine(args):
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved_gbs / hbm_peak, "traffic": None,
+                "frac": achieved_gbs / hbm_peak, "traffic": traffic,
                 "kernel": (f"k_sweeps_lp (fused: {sweeps_per_launch} correction sweeps per launch)"
                            if fused else "k_phase_lp (one correction half-sweep)"),
                 "peak_source": hbm_src}
