@@ -182,7 +182,9 @@ constexpr int64_t kMaxFusedSweeps = 1024;
 // millisecond even at m = 256; two seconds only catches a broken invariant.
 constexpr unsigned long long kFusedWaitNs = 2000000000ull;
 
-static bool fused_ok(const mc_chain* c) { return c->d.stair <= 2 && c->lay.nfar == 0; }
+// Stair splittings run fused (block-tridiagonal in place, block-banded with
+// alternating buffers); block Jacobi / Gauss-Seidel one sweep at a time.
+static bool fused_ok(const mc_chain* c) { return c->d.stair <= 2; }
 
 // n stair sweeps src -> dst (in place allowed) as fused launches of at most
 // kMaxFusedSweeps sweeps, each followed by the normalisation (with the step
@@ -196,6 +198,12 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
   const int64_t L = c->lay.L;
   const size_t cnt_bytes = sizeof(unsigned long long) + (size_t)L * sizeof(int);
   double* scale = c->flsum + 2 * L;
+  const bool banded = c->lay.nfar > 0;
+  int bw = 1;
+  for (int i = 0; i < c->lay.nfar; ++i) {
+    const int o = c->lay.far_off[i] < 0 ? -c->lay.far_off[i] : c->lay.far_off[i];
+    if (o > bw) bw = o;
+  }
   if (ev) CK(cudaEventRecord(ev[0], s));
   const double* in = src;
   for (int64_t done = 0; done < n;) {
@@ -220,15 +228,21 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     a.ms = c->lay.ms;
     a.paired = c->d.paired && !coupled;
     a.wait_ns = kFusedWaitNs;
+    a.far = banded ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
+    a.bw = bw;
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
     CK(launch_sweeps_fused(a, coupled, c->nb_fused, s));
     if (ev && final) CK(cudaEventRecord(ev[1], s));
     CK(launch_fused_scale(c->flsum, L, K, scale, scale + 2, &c->hdr->ticket[4], s));
     if (ev && final) CK(cudaEventRecord(ev[2], s));
     NormArgs nn{};
-    nn.z = c->z;
     // step error of the last sweep: z_K / s_K against z_{K-1} / s_{K-1}
-    nn.x_old = final ? (K == 1 ? in : c->xb) : nullptr;
+    // (block-tridiagonal: z_K in Z, z_{K-1} in W; block-banded: z_k in W for
+    // odd k, in Z for even k >= 2)
+    const double* last = banded ? ((K & 1) ? c->xb : c->z) : c->z;
+    const double* prev = banded ? ((K & 1) ? c->z : c->xb) : c->xb;
+    nn.z = last;
+    nn.x_old = final ? (K == 1 ? in : prev) : nullptr;
     nn.s_old = scale + 1;
     nn.x_new = dst;
     nn.s = scale;
@@ -244,10 +258,9 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
   return MC_OK;
 }
 
-// nsweeps sweeps src -> dst (in place allowed).  Stair splittings of
-// block-tridiagonal chains run as fused launches; block-banded chains (whose
-// far terms read the previous iterate in both half-sweeps) and the comparison
-// splittings run one sweep at a time, each normalised.
+// nsweeps sweeps src -> dst (in place allowed).  Stair splittings run as
+// fused launches; the comparison splittings one sweep at a time, each
+// normalised.
 static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
                           double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr) {
   if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev);
@@ -298,7 +311,7 @@ static int enqueue_lp_sweeps_fused(mc_chain* c, int64_t K, cudaStream_t s) {
   CK(launch_sweeps_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m,
                       c->d.stair == 1 ? 0 : 1, c->lay.lp_bs, c->lay.lp_cbs, c->lay.lp == 2,
                       c->d.apply == MC_APPLY_COUPLED, K, c->fver, c->fclaim, c->hdr, kFusedWaitNs,
-                      c->nb_fused, s));
+                      c->num_sms, s));
   return MC_OK;
 }
 

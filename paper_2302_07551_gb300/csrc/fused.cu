@@ -65,6 +65,43 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
   }
 }
 
+// Block-banded chains (Algorithm 2 with off-staircase terms, inverse mode):
+// every row also adds sum_d T_{l,l+d} x_{l+d} over the far diagonals |d| >= 2
+// from the sweep's input, at levels of both parities, so the sweeps cannot
+// update in place.  Y_0 = x_in; sweep k reads Y_k and writes Y_{k+1} into W
+// (k even) or Z (k odd), over Y_{k-1}.  A unit of sweep k at level l waits
+// until every level within the band l - bw .. l + bw has finished sweep k - 1
+// (its inputs are ready and every reader of the Y_{k-1} it overwrites is
+// done); a coupled-row unit also waits for half-sweep 1 of sweep k at l - 1
+// and l + 1.
+template <int R>
+__global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs a) {
+  extern __shared__ double vsh[];
+  const int lane = threadIdx.x & 31;
+  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
+  const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
+  unsigned long long q0 = claim_unit(a.claim, lane);
+  unsigned long long q = __shfl_sync(kFull, q0, 0);
+  while (q < total) {
+    q0 = claim_unit(a.claim, lane);
+    const int64_t k = (int64_t)(q / (unsigned long long)a.L);
+    const int64_t r = (int64_t)q - k * a.L;
+    const bool h2 = r >= a.P0;
+    const int64_t l = h2 ? 2 * (r - a.P0) + (1 - a.par0) : 2 * r + a.par0;
+    const double* y = k == 0 ? a.x_in : ((k & 1) ? a.W : a.Z);   // Y_k
+    double* dst = (k & 1) ? a.Z : a.W;                             // Y_{k+1}
+    if (k > 0 || h2)
+      wait_band(a.ver, l, a.L, a.bw, (int)k, (int)(h2 ? k + 1 : k), &a.hdr->status, lane,
+                a.wait_ns);
+    const double* near = h2 ? dst : y;
+    const double t = level_sweep2<R, false, false, true, true>(
+        a.A, a.B, a.C, near, near, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, a.far, y, y);
+    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+    publish(a.ver + l, (int)(k + 1), lane);
+    q = __shfl_sync(kFull, q0, 0);
+  }
+}
+
 // Self-test of the bounded wait: one warp waits for level 1 of a 3-level
 // counter array; the counters hold `preset`, the wait needs 1.
 __global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver) {
@@ -136,8 +173,37 @@ cudaError_t sweeps_r(const FusedArgs& a, int nb, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int R>
+cudaError_t banded_r(const FusedArgs& a, int nb, cudaStream_t s) {
+  static bool done = false;
+  const size_t smem = (size_t)kWarpsPerBlock * 3 * 32 * R * sizeof(double);
+  if (!done && smem > 40 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_sweeps_banded<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  k_sweeps_banded<R><<<nb, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <bool C>
 cudaError_t sweeps_dispatch(const FusedArgs& a, int nb, cudaStream_t s) {
+  if (a.far) {
+    if (C) return cudaErrorInvalidValue;   // block-banded chains: inverse mode only
+    switch ((a.m + 31) / 32) {
+      case 1: return banded_r<1>(a, nb, s);
+      case 2: return banded_r<2>(a, nb, s);
+      case 3: return banded_r<3>(a, nb, s);
+      case 4: return banded_r<4>(a, nb, s);
+      case 5: return banded_r<5>(a, nb, s);
+      case 6: return banded_r<6>(a, nb, s);
+      case 7: return banded_r<7>(a, nb, s);
+      case 8: return banded_r<8>(a, nb, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.paired && !C) {
     switch (a.m / 32) {
       case 2: return sweeps_r<2, false, true>(a, nb, s);

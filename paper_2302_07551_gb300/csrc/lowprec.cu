@@ -169,22 +169,36 @@ struct LpFused {
   unsigned long long wait_ns;
 };
 
+// Grid: every block the kernel's occupancy allows on every SM (the correction
+// sweeps are memory-latency bound, so more resident warps help), but no more
+// warps than levels.
 template <typename T, int G, int GF, bool C, int SMALL = 0>
-cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t s) {
+cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int num_sms, cudaStream_t s) {
   const size_t smem = (size_t)kWarpsPerBlock * 3 * LpSlice<T, G, GF>::SL * sizeof(float);
-  static bool done = false;
-  if (!done && smem > 40 * 1024) {
-    const cudaError_t e = cudaFuncSetAttribute(
-        k_sweeps_lp<T, G, GF, C, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  static int occ = 0;
+  if (occ == 0) {
+    if (smem > 40 * 1024) {
+      const cudaError_t e = cudaFuncSetAttribute(
+          k_sweeps_lp<T, G, GF, C, SMALL>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      if (e != cudaSuccess) return e;
+    }
+    int o = 0;
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &o, k_sweeps_lp<T, G, GF, C, SMALL>, 256, smem);
     if (e != cudaSuccess) return e;
-    done = true;
+    occ = o < 1 ? 1 : o;
   }
-  k_sweeps_lp<T, G, GF, C, SMALL><<<nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr, f.wait_ns);
+  int64_t nb = (int64_t)occ * num_sms;
+  const int64_t need = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  if (nb > need) nb = need;
+  k_sweeps_lp<T, G, GF, C, SMALL><<<(int)nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr,
+                                                              f.wait_ns);
   return cudaGetLastError();
 }
 
 template <typename T, bool C>
 cudaError_t lp_dispatch(const LpArgs& a, const LpFused& f, int nb, cudaStream_t s) {
+  // nb: the number of SMs
   constexpr int V = Pack<T>::V;
   const int G = (a.m + 32 * V - 1) / (32 * V);
   const int GF = (a.m + 63) / 64;
@@ -223,7 +237,8 @@ cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const
                              float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
                              int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
                              unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
-                             int nb, cudaStream_t s) {
+                             int num_sms, cudaStream_t s) {
+  const int nb = num_sms;
   LpArgs a{};
   a.A = A;
   a.B = B;

@@ -114,6 +114,11 @@ struct FusedArgs {
   int par0;              // 0: STAIR1, 1: STAIR2
   int paired;
   unsigned long long wait_ns;   // bound of one wait for a neighbour level
+  // block-banded chains: off-staircase diagonals (NULL: block-tridiagonal) and
+  // the band half-width bw = max |d|; the sweeps then alternate between W and
+  // Z (sweep k writes W for even k, Z for odd k) instead of updating in place
+  const FarDesc* far;
+  int bw;
 };
 
 struct NormArgs {
@@ -185,7 +190,7 @@ cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const
                              float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
                              int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
                              unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
-                             int nb, cudaStream_t s);
+                             int num_sms, cudaStream_t s);
 cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,
                           int nb, Header* hdr, double* s_out, cudaStream_t s);
 

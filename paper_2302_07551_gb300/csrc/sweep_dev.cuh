@@ -180,7 +180,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // warp's shared memory.
 // Off-staircase terms of a block-banded Q^T: acc += sum_j T_{l,l+d_j} v_{l+d_j}
 // with v = xlo for d_j < 0 and xup for d_j > 0 (staged through slice).
-template <int R>
+template <int R, bool CG = false>
 __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const FarDesc* far,
                                           const double* xlo, const double* xup, int64_t l,
                                           int64_t L, int m, int ms, double* slice, int lane) {
@@ -189,7 +189,7 @@ __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const F
     const int64_t k = l + far->off[j];
     if (k < 0 || k >= L) continue;
     __syncwarp();
-    stage_vec<R>(slice, (far->off[j] < 0 ? xlo : xup) + k * m, m, lane);
+    stage_vec<R, CG>(slice, (far->off[j] < 0 ? xlo : xup) + k * m, m, lane);
     __syncwarp();
     gemv_acc<R>(acc, far->plane[j] + (size_t)l * ms, slice, m, lane);
   }
@@ -224,7 +224,7 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
     if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
     if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
   }
-  if (far) far_terms<R>(acc, far, xfar_lo, xfar_up, l, L, m, ms, v_lo, lane);
+  if (far) far_terms<R, CG>(acc, far, xfar_lo, xfar_up, l, L, m, ms, v_lo, lane);
   if (!COUPLED) {
 #pragma unroll
     for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);

@@ -60,6 +60,35 @@ __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64
   if (up) (void)ld_acquire(ver + l + 1);
 }
 
+// Block-banded dataflow: wait until every level j in [l - bw, l + bw] has
+// completed `need` writes and, when near_need > need, levels l - 1 and l + 1
+// have completed near_need; lane i polls level l - bw + i (2 bw + 1 <= 32).
+// Afterwards every lane acquires all of them itself (its reads of any of these
+// levels are ordered after the producers' writes).  Bounded like
+// wait_neighbours.
+__device__ __forceinline__ void wait_band(const int* ver, int64_t l, int64_t L, int bw, int need,
+                                          int near_need, int* status, int lane,
+                                          unsigned long long wait_ns) {
+  const int64_t j = l - bw + lane;
+  const bool mine = lane <= 2 * bw && j >= 0 && j < L;
+  const int nj = (j == l - 1 || j == l + 1) ? near_need : need;
+  bool ok = !mine || ld_acquire(ver + j) >= nj;
+  if (!__all_sync(0xffffffffu, ok)) {
+    const unsigned long long t0 = global_ns();
+    while (true) {
+      __nanosleep(128);
+      if (!ok) ok = ld_acquire(ver + j) >= nj;
+      if (__all_sync(0xffffffffu, ok)) break;
+      if (__any_sync(0xffffffffu, global_ns() - t0 > wait_ns)) {
+        if (lane == 0) atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+  for (int64_t i = l - bw; i <= l + bw; ++i)
+    if (i >= 0 && i < L) (void)ld_acquire(ver + i);
+}
+
 // Level l now holds its version v: every lane's stores of z_l are made
 // visible before the counter.
 __device__ __forceinline__ void publish(int* ver, int v, int lane) {

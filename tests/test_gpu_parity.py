@@ -451,6 +451,35 @@ def test_banded_sweeps_residual_and_solve(L, m, p, q):
     ch.close()
 
 
+@pytest.mark.parametrize("stair", [1, 2])
+def test_banded_fused_stats_and_in_place(stair):
+    """Block-banded fused launches alternate two buffers: e^T z of the last
+    sweep (relative to the previous iterate) and the step error after K = 1,
+    2, 3 and 9 sweeps, in place and out of place, as the oracle's."""
+    L, m, p, q = 26, 24, 2, 4
+    D = synth.banded(L, m, p, q, 0.8, seed=7)
+    bc = oracle.BandedChain(D)
+    meth = oracle.STAIR1 if stair == 1 else oracle.STAIR2
+    ch = mc.Chain.banded({e: dev(B) for e, B in D.items()}, stair=stair)
+    N = L * m
+    x0 = np.random.default_rng(9).random(N)
+    x0 /= x0.sum()
+    for K in (1, 2, 3, 9):
+        prev = bc.sweeps(x0, K - 1, method=meth) if K > 1 else x0
+        z = bc.sweep(prev, method=meth)
+        ref = z / z.sum()
+        for in_place in (False, True):
+            x = dev(x0.copy())
+            st = torch.zeros(3, dtype=torch.float64, device="cuda")
+            out = ch.sweep(x, x if in_place else None, nsweeps=K, stats=st)
+            assert rel_l1(out.cpu().numpy(), ref) <= 1e-12, (K, in_place)
+            s, d = st.cpu().numpy()[:2]
+            assert abs(s - z.sum()) <= 1e-12 * abs(z.sum())
+            assert abs(d - np.abs(ref - prev).sum()) <= 1e-12
+    ch.sync()
+    ch.close()
+
+
 def test_banded_restrictions():
     D = {e: dev(B) for e, B in synth.banded(8, 8, 1, 3, 0.8, seed=1).items()}
     for kw in (dict(apply="coupled"), dict(dtype="f32")):
