@@ -30,11 +30,18 @@ __device__ __forceinline__ int find_req(const int64_t* off, int lo, int hi, int6
   return lo;
 }
 
-// Item range and request range of a bucket.
+// Item range and request range of a bucket: m <= 128 or m > 128 (large), or
+// for the low-precision kernels (lp_class 0, 1, 2) m <= 64, 64 < m <= 128,
+// m > 128.
 __device__ __forceinline__ void bucket(const BTable* t, const int64_t* off, bool large, int& r0,
-                                       int& r1, int64_t& i0, int64_t& i1) {
-  r0 = large ? t->n_small : 0;
-  r1 = large ? t->n : t->n_small;
+                                       int& r1, int64_t& i0, int64_t& i1, int lp_class = -1) {
+  if (lp_class >= 0) {
+    r0 = lp_class == 0 ? 0 : lp_class == 1 ? t->n_tiny : t->n_small;
+    r1 = lp_class == 0 ? t->n_tiny : lp_class == 1 ? t->n_small : t->n;
+  } else {
+    r0 = large ? t->n_small : 0;
+    r1 = large ? t->n : t->n_small;
+  }
   i0 = off[r0];
   i1 = off[r1];
 }
@@ -260,17 +267,20 @@ __global__ void __launch_bounds__(256) k_b_zero_d(const BTable* __restrict__ t) 
 // m <= 128 (G = GF = 2, FP32 or two-row BF16); large bucket m <= 256
 // (FP32 G = 4, four-row BF16 G = 2; GF = 4).  All K correction sweeps of a
 // refinement step in one launch per bucket, d in place.
-template <typename TS, typename TL, bool COUPLED, bool LARGE>
+// CLS: 0 -> m <= 64, 1 -> 64 < m <= 128, 2 -> m > 128 (one kernel per class,
+// so that each has the register count of its own path).
+template <typename TS, typename TL, bool COUPLED, int CLS>
 __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ t, int K,
                                                      unsigned long long* claim, BOut* out) {
   extern __shared__ float fsh[];
+  constexpr bool LARGE = CLS == 2;
   constexpr int SL = LARGE ? 256 : 128;
   const int lane = threadIdx.x & 31;
   float* slice = fsh + (threadIdx.x >> 5) * 3 * SL;
   int r0, r1;
   int64_t a0, a1, b0, b1;
-  bucket(t, t->off_h1, LARGE, r0, r1, a0, a1);
-  bucket(t, t->off_h2, LARGE, r0, r1, b0, b1);
+  bucket(t, t->off_h1, LARGE, r0, r1, a0, a1, CLS);
+  bucket(t, t->off_h2, LARGE, r0, r1, b0, b1, CLS);
   const int64_t n1 = a1 - a0, U = n1 + (b1 - b0);
   if (U == 0) return;
   const unsigned long long total = (unsigned long long)K * (unsigned long long)U;
@@ -284,12 +294,16 @@ __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ 
     if (u.h2 || u.k > 0)
       wait_neighbours(Q->ver, u.l, Q->L, base + (int)(u.h2 ? u.k + 1 : u.k), &out[u.r].status,
                       lane, kWaitNs);
-    if (LARGE) {
+    if constexpr (CLS == 2) {
       constexpr int G = Pack<TL>::V == 2 ? 4 : 2;
       level_sweep_lp<TL, G, 4, COUPLED, true>((const TL*)Q->lA, (const TL*)Q->lB, Q->lC, Q->sc,
                                               Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
                                               slice, lane);
-    } else if (Q->m <= 64 && (sizeof(TS) == 4 || Q->m % 8 == 0)) {
+    } else if constexpr (CLS == 1) {
+      level_sweep_lp<TS, 2, 2, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
+                                              Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
+                                              slice, lane);
+    } else if (sizeof(TS) == 4 || Q->m % 8 == 0) {
       // 16-byte lane loads (BF16 columns 16-byte aligned when m % 8 == 0)
       using S = typename std::conditional<sizeof(TS) == 4 && !std::is_same<TS, Bf16x2>::value,
                                           float, unsigned short>::type;
@@ -305,12 +319,8 @@ __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ 
         level_sweep_lp_small<S, 64, COUPLED, true>((const S*)Q->lA, (const S*)Q->lB, Q->lC, Q->sc,
                                                    Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs,
                                                    Q->lp_cbs, slice, lane);
-    } else if (Q->m <= 64) {
-      level_sweep_lp<TS, 1, 1, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
-                                              Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
-                                              slice, lane);
     } else {
-      level_sweep_lp<TS, 2, 2, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
+      level_sweep_lp<TS, 1, 1, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC, Q->sc,
                                               Q->d, Q->q, u.l, Q->L, Q->m, Q->lp_bs, Q->lp_cbs,
                                               slice, lane);
     }
@@ -342,10 +352,11 @@ cudaError_t lp_pair(const BTable* t, unsigned long long* claim, BOut* out, int K
                     cudaStream_t s) {
   const size_t sm_small = (size_t)(g.threads / 32) * 3 * 128 * sizeof(float);
   const size_t sm_large = (size_t)(g.threads / 32) * 3 * 256 * sizeof(float);
-  cudaError_t e = allow(k_b_sweeps_lp<TS, TL, C, true>, sm_large);
+  cudaError_t e = allow(k_b_sweeps_lp<TS, TL, C, 2>, sm_large);
   if (e != cudaSuccess) return e;
-  k_b_sweeps_lp<TS, TL, C, false><<<g.blocks, g.threads, sm_small, s>>>(t, K, claim, out);
-  k_b_sweeps_lp<TS, TL, C, true><<<g.blocks, g.threads, sm_large, s>>>(t, K, claim + 1, out);
+  k_b_sweeps_lp<TS, TL, C, 0><<<g.blocks, g.threads, sm_small, s>>>(t, K, claim, out);
+  k_b_sweeps_lp<TS, TL, C, 1><<<g.blocks, g.threads, sm_small, s>>>(t, K, claim + 1, out);
+  k_b_sweeps_lp<TS, TL, C, 2><<<g.blocks, g.threads, sm_large, s>>>(t, K, claim + 2, out);
   return cudaGetLastError();
 }
 

@@ -6,7 +6,9 @@
 // so one captured CUDA graph serves any active set.  Requests are ordered
 // small blocks first (m <= 128: rows per lane R <= 4) and large blocks after
 // (m <= 256: R = 8); each bucket has its own kernel so that register use
-// follows the bucket.
+// follows the bucket.  The low-precision kernels split the small bucket once
+// more: m <= 64 (16-byte-load path, few registers, more resident warps) and
+// 64 < m <= 128.
 //
 // Every reduction is per level first (one partial per level), then per
 // request in level order: a request's iterates do not depend on which other
@@ -54,9 +56,9 @@ struct BReq {
 struct BTable {
   int32_t n;            // active requests
   int32_t n_small;      // requests [0, n_small) have m <= 128
+  int32_t n_tiny;       // requests [0, n_tiny) have m <= 64 (low-precision kernels only)
   int32_t epoch;        // completion-counter base of this chunk
-  int32_t pad;
-  unsigned long long claim[2];   // queue counters of the small / large bucket (0 in t_host)
+  unsigned long long claim[3];   // queue counters of the buckets of one chunk (0 in t_host)
   int64_t off_h1[kMaxReq + 1];   // prefix counts of half-sweep-1 levels
   int64_t off_h2[kMaxReq + 1];   // prefix counts of half-sweep-2 levels
   int64_t off_lv[kMaxReq + 1];   // prefix counts of all levels

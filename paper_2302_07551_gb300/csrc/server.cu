@@ -225,7 +225,7 @@ uint64_t signature(const mc_server* s) {
   int lg = 0;
   while ((1LL << lg) < lv && lg < 62) ++lg;
   return ((uint64_t)(t->n_small > 0) << 0) | ((uint64_t)(t->n > t->n_small) << 1) |
-         ((uint64_t)(lg / 2) << 8);
+         ((uint64_t)(t->n_tiny > 0) << 2) | ((uint64_t)(lg / 2) << 8);
 }
 
 // Factor status of newly admitted requests (one sync when there are any).
@@ -257,18 +257,21 @@ int check_fresh(mc_server* s) {
 // Fill the pinned request table from the active list (small blocks first);
 // returns the table order.
 std::vector<Req*> build_table(mc_server* s) {
-  std::stable_sort(s->active.begin(), s->active.end(), [](const Req* a, const Req* b) {
-    return (a->chain->lay.m > 128) < (b->chain->lay.m > 128);
-  });
+  // size classes m <= 64, 64 < m <= 128, m > 128, in that order
+  auto cls = [](const Req* r) { return r->chain->lay.m > 128 ? 2 : r->chain->lay.m > 64 ? 1 : 0; };
+  std::stable_sort(s->active.begin(), s->active.end(),
+                   [&](const Req* a, const Req* b) { return cls(a) < cls(b); });
   BTable* t = s->t_host;
   t->n = (int32_t)s->active.size();
   t->n_small = 0;
+  t->n_tiny = 0;
   t->off_h1[0] = t->off_h2[0] = t->off_lv[0] = 0;
   const int p1 = s->d.stair == 1 ? 0 : 1;
   for (int i = 0; i < t->n; ++i) {
     const Req* r = s->active[(size_t)i];
     const int64_t L = r->chain->lay.L;
     if (r->chain->lay.m <= 128) t->n_small = i + 1;
+    if (r->chain->lay.m <= 64) t->n_tiny = i + 1;
     fill_req(s, r, &t->r[i]);
     t->off_h1[i + 1] = t->off_h1[i] + (L - p1 + 1) / 2;
     t->off_h2[i + 1] = t->off_h2[i] + (L - (1 - p1) + 1) / 2;
@@ -427,15 +430,18 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
     const uint64_t sig = signature(s);
     auto it = s->tuned.find(sig);
     if (it == s->tuned.end() && s->d.autotune) {
-      // candidates: 1..4 resident 256-thread blocks per SM; each runs one
-      // full chunk on the live set (real work, counted as such); tuning of
-      // this signature ends early when the active set changes
+      // candidates: 1, 2, 3, 4, 6, 8 resident 256-thread blocks per SM (the
+      // low-precision kernels of small blocks have the registers for 8);
+      // each runs one full chunk on the live set (real work, counted as
+      // such); tuning of this signature ends early when the active set changes
       float best = 1e30f;
       BGrid bestg = s->g_grid;
       cudaEvent_t e0 = nullptr, e1 = nullptr;
       if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
         return MC_ERR_CUDA;
-      for (int k = 1; k <= 4 && rc == MC_OK; ++k) {
+      static const int kCand[] = {1, 2, 3, 4, 6, 8};
+      for (int ci = 0; ci < 6 && rc == MC_OK; ++ci) {
+        const int k = kCand[ci];
         const BGrid gk{k * s->num_sms, 256};
         if (cudaEventRecord(e0, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
         if (rc == MC_OK) {
