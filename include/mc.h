@@ -195,8 +195,11 @@ int mc_sweep(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps
 
 /*
  * As mc_sweep but with HOST vectors (pinned memory recommended): copies
- * x_in_host to the device, sweeps, copies the result to x_out_host and
- * stats (3 doubles, may be NULL) to stats_host.  Syncs.
+ * x_in_host to the device, sweeps, and returns the result in x_out_host and
+ * stats (3 doubles, may be NULL) in stats_host.  When x_out_host is
+ * page-locked (cudaHostAlloc / cudaHostRegister) and the sweeps run as one
+ * fused launch, the normalisation stores the result into it directly;
+ * otherwise the result is copied back.  Syncs.
  */
 int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, int64_t nsweeps,
                   double* stats_host);

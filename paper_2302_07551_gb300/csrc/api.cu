@@ -605,10 +605,22 @@ int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int6
   if (!c || !x_in_host || !x_out_host || nsweeps < 1) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
   const size_t bytes = (size_t)c->lay.N * sizeof(double);
+  // page-locked output buffer: the final normalisation stores the result
+  // straight into it (one fused launch; no separate device-to-host copy)
+  double* out_dev = nullptr;
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, x_out_host) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer &&
+        ((uintptr_t)pa.devicePointer & 15u) == 0 && fused_ok(c) && nsweeps <= kMaxFusedSweeps)
+      out_dev = (double*)pa.devicePointer;
+  } else {
+    cudaGetLastError();
+  }
   CK(cudaMemcpyAsync(c->xa, x_in_host, bytes, cudaMemcpyHostToDevice, c->user));
-  const int rc = enqueue_sweeps(c, c->xa, c->xa, nsweeps, nullptr, c->user);
+  const int rc = enqueue_sweeps(c, c->xa, out_dev ? out_dev : c->xa, nsweeps, nullptr, c->user);
   if (rc != MC_OK) return rc;
-  CK(cudaMemcpyAsync(x_out_host, c->xa, bytes, cudaMemcpyDeviceToHost, c->user));
+  if (!out_dev)
+    CK(cudaMemcpyAsync(x_out_host, c->xa, bytes, cudaMemcpyDeviceToHost, c->user));
   const int st = sync_header(c);
   if (stats_host) {
     stats_host[0] = c->hh->stats[0];

@@ -411,6 +411,31 @@ def test_in_place_single_and_multi_sweep():
     ch.close()
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_sweeps_equal_device_sweeps(pinned):
+    """mc_sweep_host (pinned output: the normalisation writes it directly;
+    pageable: copied back) gives bitwise the device call's iterate and stats,
+    in place and out of place."""
+    L, m = 37, 24
+    blocks, _ = make(L, m, seed=12)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    N = L * m
+    x0 = torch.rand(N, dtype=torch.float64)
+    x0 /= x0.sum()
+    for n in (1, 4):
+        st = torch.zeros(3, dtype=torch.float64, device="cuda")
+        ref = ch.sweep(x0.cuda(), nsweeps=n, stats=st).cpu()
+        xh = x0.clone().pin_memory() if pinned else x0.clone()
+        yh = torch.empty(N, dtype=torch.float64)
+        yh = yh.pin_memory() if pinned else yh
+        sh = ch.sweep_host(xh, yh, n)
+        assert torch.equal(yh, ref) and sh[0] == float(st[0]) and sh[1] == float(st[1])
+        sh = ch.sweep_host(xh, xh, n)                     # in place
+        assert torch.equal(xh, ref)
+    ch.sync()
+    ch.close()
+
+
 def test_bounded_wait_reports_instead_of_hanging():
     """The wait between units of a fused launch gives up after its limit and
     latches MC_ERR_TIMEOUT; a satisfiable wait returns at once."""
