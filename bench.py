@@ -313,23 +313,16 @@ def run_mine(args):
     # dominant kernel: the fused sweep kernel (one launch runs all timed
     # sweeps, up to 1024 per launch) or, for the low-precision correction
     # sweeps, one half-sweep launch
-    fused = prof.get("fused", False)
-    if fused:
-        sweeps_per_launch = min(prof_steps, 1024)
-        n_launch = -(-prof_steps // 1024)
-        kern_ms = prof["sweeps_ms"] / n_launch
-        kern_bytes = bytes_level * L * sweeps_per_launch
-        kern_flops = flops_level * L * sweeps_per_launch
-        kern_ms_per_sweep = {"sweeps": prof["sweeps_ms"] / prof_steps,
-                             "scale": prof["scale_ms"] / prof_steps,
-                             "normalise": prof["norm_ms"] / prof_steps}
-    else:
-        kern_ms = (prof["half1_ms"] + prof["half2_ms"]) / (2 * prof_steps)
-        kern_bytes = bytes_level * L / 2
-        kern_flops = flops_level * L / 2
-        kern_ms_per_sweep = {"half1": prof["half1_ms"] / prof_steps,
-                             "half2": prof["half2_ms"] / prof_steps,
-                             "normalise": prof["norm_ms"] / prof_steps}
+    # (every stair sweep runs fused: up to 1024 sweeps per launch)
+    fused = prof["fused"]
+    sweeps_per_launch = min(prof_steps, 1024) if fused else 1
+    n_launch = -(-prof_steps // sweeps_per_launch)
+    kern_ms = prof["sweeps_ms"] / n_launch
+    kern_bytes = bytes_level * L * sweeps_per_launch
+    kern_flops = flops_level * L * sweeps_per_launch
+    kern_ms_per_sweep = {"sweeps": prof["sweeps_ms"] / prof_steps,
+                         "scale": prof["scale_ms"] / prof_steps,
+                         "normalise": prof["norm_ms"] / prof_steps}
     hbm_peak, hbm_src = peaks()
     achieved_gbs = kern_bytes / (kern_ms * 1e-3) / 1e9
     achieved_tf = kern_flops / (kern_ms * 1e-3) / 1e12
@@ -342,7 +335,7 @@ def run_mine(args):
         rate, cores, sample, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
     if args.dtype == "f64":
-        kname = "k_sweeps" if fused else "k_phase"
+        kname = ("k_sweeps_banded" if banded else "k_sweeps") if fused else "k_phase"
         key = f"{name}:{args.apply}"
     else:
         kname = "k_sweeps_lp"
@@ -360,16 +353,14 @@ def run_mine(args):
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic,
-                "kernel": (f"k_sweeps (fused: {sweeps_per_launch} sweeps per launch)" if fused
-                           else "k_phase (one half-sweep)"),
+                "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps per launch)",
                 "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (rate measured, profiles/fp64_peak.md)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
         roof = {"bound": "hbm", "achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                 "frac": achieved_gbs / hbm_peak, "traffic": traffic,
-                "kernel": (f"k_sweeps_lp (fused: {sweeps_per_launch} correction sweeps per launch)"
-                           if fused else "k_phase_lp (one correction half-sweep)"),
+                "kernel": f"k_sweeps_lp (fused: {sweeps_per_launch} correction sweeps per launch)",
                 "peak_source": hbm_src}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -226,8 +226,9 @@ int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns);
  *   fused sweeps (ms_host[4] = 1): [0] the fused sweep kernel(s) with their
  *     counter reset, [1] the reduction of e^T z, [2] the normalisation (both
  *     0 for low-precision chains), [3] launches;
- *   otherwise (ms_host[4] = 0): [0] half-sweep 1, [1] half-sweep 2, [2] the
- *     normalisations, summed over the sweeps, [3] launches.
+ *   comparison splittings, desc.stair 3 or 4 (ms_host[4] = 0): [0] the
+ *     sweeps, [1] 0, [2] the normalisations, summed over the sweeps,
+ *     [3] launches.
  * 1 <= nsweeps <= 2^20.  Syncs.
  */
 int mc_profile(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps,

@@ -102,10 +102,7 @@ class Chain:
         ms = (ctypes.c_double * 5)()
         nat.check(self._lib.mc_profile(self._h, _ptr(x_in), _ptr(x_out), int(nsweeps), ms),
                   "mc_profile")
-        if ms[4] == 1.0:
-            return x_out, dict(fused=True, sweeps_ms=ms[0], scale_ms=ms[1], norm_ms=ms[2],
-                               launches=int(ms[3]))
-        return x_out, dict(fused=False, half1_ms=ms[0], half2_ms=ms[1], norm_ms=ms[2],
+        return x_out, dict(fused=ms[4] == 1.0, sweeps_ms=ms[0], scale_ms=ms[1], norm_ms=ms[2],
                            launches=int(ms[3]))
 
     def sweep_host(self, x_in, x_out, nsweeps=1):

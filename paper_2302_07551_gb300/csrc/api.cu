@@ -96,70 +96,42 @@ using namespace mc;
     if ((call) != cudaSuccess) return MC_ERR_CUDA; \
   } while (0)
 
-// Enqueue one sweep as separate launches (block-banded chains, block Jacobi /
-// Gauss-Seidel): the half-sweeps, then the normalisation into dst with the
-// step error.  ev (optional) = 4 events recorded before half-sweep 1, between
-// the half-sweeps, before and after the normalisation.
+// One sweep of a comparison splitting of Sect. 2 (the stair splittings run
+// fused): block Jacobi (every level from x, one launch) or block Gauss-Seidel
+// (levels in order, one warp), then the normalisation into dst with the step
+// error.  ev (optional) = 4 events recorded before the sweep, twice after it,
+// and after the normalisation.
 static int enqueue_sweep(mc_chain* c, const double* src, double* dst, double* stats_out,
                          cudaStream_t s, cudaEvent_t* ev = nullptr) {
-  const int64_t L = c->lay.L;
-  const int p1 = c->d.stair == 1 ? 0 : 1;   // 0-based parity of the diagonal-only rows
-  const int p2 = 1 - p1;
   const bool coupled = c->d.apply == MC_APPLY_COUPLED;
   const size_t pe = c->lay.plane_bytes / sizeof(double);
   PhaseArgs a{};
   a.A = c->planes + (coupled ? kPlaneWLO : kPlaneTLO) * pe;
   a.B = c->planes + (coupled ? kPlaneWUP : kPlaneTUP) * pe;
   a.C = c->planes + kPlaneNINV * pe;
-  a.L = L;
+  a.L = c->lay.L;
   a.m = c->lay.m;
   a.ms = c->lay.ms;
-  a.stride = 2;
   a.far = c->lay.nfar ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
   a.xfar = src;
-  if (c->d.stair >= 3) {
-    // comparison splittings of Sect. 2: block Jacobi (every level from x, one
-    // launch) and block Gauss-Seidel (levels in order, one warp)
-    a.src = src;
-    a.src_up = src;
-    a.dst = c->z;
-    a.wpart = c->wpart;
-    a.hdr = c->hdr;
-    a.parity = 0;
-    a.stride = 1;
-    a.P = L;
-    a.reduce_s = 1;
-    a.n_wpart = c->nw;
-    if (ev) CK(cudaEventRecord(ev[0], s));
-    if (c->d.stair == 3) {
-      CK(launch_phase(a, coupled, c->nb_phase, s));
-    } else {
-      CK(launch_bgs(a, coupled, s));
-    }
-    if (ev) CK(cudaEventRecord(ev[1], s));
-    if (ev) CK(cudaEventRecord(ev[2], s));
-  } else {
-  // half-sweep 1: diagonal-only rows read x at their neighbours
   a.src = src;
+  a.src_up = src;
   a.dst = c->z;
   a.wpart = c->wpart;
-  a.parity = p1;
-  a.P = (L - p1 + 1) / 2;
   a.hdr = c->hdr;
-  a.reduce_s = 0;
-  a.n_wpart = 2 * c->nw;
+  a.parity = 0;
+  a.stride = 1;
+  a.P = c->lay.L;
+  a.reduce_s = 1;
+  a.n_wpart = c->nw;
   if (ev) CK(cudaEventRecord(ev[0], s));
-  CK(launch_phase(a, coupled, c->nb_phase, s));
-  if (ev) CK(cudaEventRecord(ev[1], s));
-  // half-sweep 2: coupled rows read the fresh z of their neighbours
-  a.src = c->z;
-  a.wpart = c->wpart + c->nw;
-  a.parity = p2;
-  a.P = (L - p2 + 1) / 2;
-  a.reduce_s = 1;   // its last block sums the partials of both half-sweeps
-  CK(launch_phase(a, coupled, c->nb_phase, s));
-  if (ev) CK(cudaEventRecord(ev[2], s));
+  if (c->d.stair == 3) {
+    CK(launch_phase(a, coupled, c->nb_phase, s));
+  } else {
+    CK(launch_bgs(a, coupled, s));
   }
+  if (ev) CK(cudaEventRecord(ev[1], s));
+  if (ev) CK(cudaEventRecord(ev[2], s));
   NormArgs n{};
   n.z = c->z;
   n.x_old = src;
@@ -587,15 +559,14 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   ms_host[1] = t[1];
   ms_host[2] = t[2];
   // kernel launches: fused chains 3 per launch of up to kMaxFusedSweeps
-  // sweeps (sweeps, scale, normalisation); otherwise 2 per sweep (1 for the
-  // comparison splittings) plus one normalisation per sweep
-  const double per = c->d.stair <= 2 ? 2.0 : 1.0;
+  // sweeps (sweeps, scale, normalisation); the comparison splittings 2 per
+  // sweep
   if (c->lay.lp)
     ms_host[3] = 2.0;   // residual (r, q) + the fused correction sweeps
   else if (fused)
     ms_host[3] = 3.0 * (double)((nsweeps + kMaxFusedSweeps - 1) / kMaxFusedSweeps);
   else
-    ms_host[3] = per * (double)nsweeps + (double)nsweeps;
+    ms_host[3] = 2.0 * (double)nsweeps;   // comparison splitting sweep + normalisation
   ms_host[4] = fused ? 1.0 : 0.0;
   return sync_header(c);
 }

@@ -34,7 +34,10 @@ namespace {
 
 using namespace dev;
 
-template <int R, bool COUPLED, bool PAIRED>
+// One block Jacobi sweep (stride 1: every level from x) or one half-sweep
+// (stride 2) per launch; used for the block Jacobi comparison splitting (the
+// stair splittings run fused, fused.cu).
+template <int R, bool COUPLED>
 __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   extern __shared__ double vsh[];
   __shared__ double red[32];
@@ -46,7 +49,7 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_phase(PhaseArgs a) {
   double wsum = 0.0;
   for (int64_t u = gw; u < a.P; u += nw) {
     const int64_t l = a.stride * u + a.parity;
-    wsum += level_sweep2<R, COUPLED, PAIRED, false>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L,
+    wsum += level_sweep2<R, COUPLED, false, false>(a.A, a.B, a.C, a.src, a.src, a.dst, l, a.L,
                                                     a.m, a.ms, slice, lane, 1.0, a.far, a.xfar,
                                                     a.xfar);
   }
@@ -265,12 +268,12 @@ cudaError_t allow_smem(K kernel, size_t bytes, bool& done) {
   return e;
 }
 
-template <int R, bool C, bool P = false>
+template <int R, bool C>
 cudaError_t phase_r(const PhaseArgs& a, int nb, cudaStream_t s) {
   static bool done = false;
-  const cudaError_t e = allow_smem(k_phase<R, C, P>, vec_smem<R>(), done);
+  const cudaError_t e = allow_smem(k_phase<R, C>, vec_smem<R>(), done);
   if (e != cudaSuccess) return e;
-  k_phase<R, C, P><<<nb, 256, vec_smem<R>(), s>>>(a);
+  k_phase<R, C><<<nb, 256, vec_smem<R>(), s>>>(a);
   return cudaGetLastError();
 }
 

@@ -247,15 +247,6 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
   return total;
 }
 
-template <int R, bool COUPLED, bool PAIRED = false>
-__device__ __forceinline__ double level_sweep(const double* A, const double* B, const double* C,
-                                              const double* src, double* dst, int64_t l,
-                                              int64_t L, int m, int ms, double* slice, int lane,
-                                              double scale = 1.0) {
-  return level_sweep2<R, COUPLED, PAIRED>(A, B, C, src, src, dst, l, L, m, ms, slice, lane,
-                                          scale);
-}
-
 // One level of the direct residual r_l = (Q^T x)_l = T_lo x_{l-1} + T_dd x_l +
 // T_up x_{l+1} (Eq. (1)); returns ||r_l||_1 on every lane.  With q != NULL
 // also stores q_l = (-T_dd)^{-1} r_l in FP32.
