@@ -175,7 +175,7 @@ def run_reference(args):
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps / (Ls / L), "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if args.dtype == "f64" else f"{args.dtype} blocks, f32 sweeps, f64 refinement", "data": "synthetic",
+           "dtype": "f64", "data": "synthetic",
            "config": {"workload": name, "L": L, "m": m, "sample_levels": Ls},
            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                             "sample": sample},

@@ -66,3 +66,27 @@ def test_reference_arm_silent_on_other_ranks(monkeypatch, capsys):
         workload, steps, warmup = "qbd_L64_m8", 3, 3
     bench.run_reference(A())
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line_on_rank0(monkeypatch, capsys):
+    """The reference arm (the oracle on the host cores) prints the contract's
+    JSON line on rank 0: impl, metric, unit, the timing keys, cpu_baseline and
+    an e2e with zero transfer bytes."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    monkeypatch.setenv("RANK", "0")
+
+    class A:
+        workload, steps, warmup, dtype = "qbd_L64_m8", 3, 1, "f64"
+    bench.run_reference(A())
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config",
+              "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["value"] > 0 and line["steps"] == 3
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
+    assert line["config"]["workload"] == "qbd_L64_m8"
