@@ -311,9 +311,7 @@ def run_mine(args):
         sweep_bytes = L * bytes_level
     flops_level = int(2 * (2.5 if (paired and args.dtype == "f64") else nmat) * m * m)
     # dominant kernel: the fused sweep kernel (one launch runs all timed
-    # sweeps, up to 1024 per launch) or, for the low-precision correction
-    # sweeps, one half-sweep launch
-    # (every stair sweep runs fused: up to 1024 sweeps per launch)
+    # sweeps or correction sweeps, up to 1024 per launch)
     fused = prof["fused"]
     sweeps_per_launch = min(prof_steps, 1024) if fused else 1
     n_launch = -(-prof_steps // sweeps_per_launch)

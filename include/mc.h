@@ -304,14 +304,15 @@ int mc_residual_noalloc(const double* dn, const double* loc, const double* up, i
  * (mc_server_request_bytes each) and at most max_active are running.  Each
  * mc_server_step runs check_every sweeps (dtype MC_F64) or one refinement
  * step of check_every correction sweeps (MC_F32 / MC_BF16) for ALL active
- * requests in shared persistent launches (one per half-sweep and block-size
- * bucket), then every request's FP64 residual; requests with residual <= tol
+ * requests in shared fused persistent launches (one per block-size bucket
+ * for all sweeps of the step), then every request's FP64 residual; requests with residual <= tol
  * (or a latched error, or maxit sweeps) are retired, their pi copied to host
  * memory and their arena memory freed.  Requests submitted between steps
  * join the next chunk.  A request's iterates are bitwise independent of the
  * other requests in the batch and of the launch grid.  With autotune = 1 the
  * first chunk of every new batch signature times candidate persistent grids
- * (1-4 resident blocks per SM) on the live requests and keeps the fastest.
+ * (1, 2, 3, 4, 6, 8 resident blocks per SM) on the live requests and keeps
+ * the fastest.
  * --------------------------------------------------------------------------- */
 typedef struct mc_server mc_server;
 

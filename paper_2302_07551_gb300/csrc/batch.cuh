@@ -1,7 +1,8 @@
 // Batched (multi-request) sweep: descriptors shared by batch.cu and server.cu.
 //
-// All active requests of the solve server advance together: one persistent
-// launch per half-sweep covers every level of every request.  The request
+// All active requests of the solve server advance together: one fused
+// persistent launch per block-size bucket covers every level of every
+// request for all sweeps of a chunk (details below).  The request
 // table lives in device memory and is rewritten by the host between chunks,
 // so one captured CUDA graph serves any active set.  Requests are ordered
 // small blocks first (m <= 128: rows per lane R <= 4) and large blocks after
