@@ -199,8 +199,9 @@ def test_errors_reported():
     with pytest.raises(mc.McError) as e:
         ch.solve(tol=1e-12, maxit=64, check_every=8)
     assert e.value.status == 6
-    # the latch was cleared: the next call works
-    assert ch.residual(x) >= 0 or True
+    # the latch was cleared: the next call runs without raising (its value is
+    # NaN, the blocks hold a NaN)
+    ch.residual(x)
     ch.close()
 
 
