@@ -352,7 +352,7 @@ def run_mine(args):
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic,
                 "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps per launch)",
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (rate measured, profiles/fp64_peak.md)",
+                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz (the pipe rate from ncu's FP64-pipe utilisation of this kernel, profiles/fp64_peak.md)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
@@ -545,10 +545,34 @@ def run_contraction(args):
 
 
 def measure_fp64_peak():
-    """FP64 multiply-add peak of this GPU: cuBLAS DGEMM 8192^3, best of 10,
-    with the SM clock sampled meanwhile."""
+    """FP64 multiply-add peak of this GPU: an fma-loop kernel of the library
+    (mc_fp64_rate: 8 independent chains per thread, 1-8 blocks of 128-512
+    threads per SM, best of the grid shapes) and cuBLAS DGEMM 8192^3 (best of
+    10), with the SM clock sampled meanwhile; the per-SM rate follows from the
+    loop's TFLOP/s, the SM count and the median SM clock."""
+    import ctypes
+
     import torch
+
+    from paper_2302_07551_gb300 import _native as nat
     torch.cuda.set_device(0)
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    lib = nat.load()
+    stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    loop = []
+    sampler = ClockSampler(0)
+    sampler.start()
+    for reg in (1, 0):
+        for per_sm in (1, 2, 4, 8):
+            for threads in (128, 256, 512):
+                v = ctypes.c_double(0.0)
+                nat.check(lib.mc_fp64_rate(stream, per_sm * sms, threads, 1 << 16, reg,
+                                           ctypes.byref(v)), "mc_fp64_rate")
+                loop.append({"blocks": per_sm * sms, "threads": threads, "reg_operands": reg,
+                             "tflops": v.value})
+    loop_clocks = sampler.stop()
+    best_loop = max(r["tflops"] for r in loop)
+    mhz = loop_clocks.get("sm_mhz") or 0.0
     n = 8192
     a = torch.rand(n, n, dtype=torch.float64, device="cuda")
     b = torch.rand(n, n, dtype=torch.float64, device="cuda")
@@ -566,7 +590,11 @@ def measure_fp64_peak():
         torch.cuda.synchronize()
         best = max(best, 2 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
     clocks = sampler.stop()
-    print(json.dumps({"fp64_dgemm_tflops": best, "n": n, "clocks": clocks}), flush=True)
+    per_sm_clk = best_loop * 1e12 / (2 * sms * mhz * 1e6) if mhz else None
+    print(json.dumps({"fp64_fma_loop_tflops": best_loop, "fma_loop_clocks": loop_clocks,
+                      "sms": sms, "dfma_lanes_per_clk_per_sm": per_sm_clk,
+                      "fp64_dgemm_tflops": best, "n": n, "clocks": clocks,
+                      "fma_loop_grid": loop}), flush=True)
 
 
 def main():
