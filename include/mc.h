@@ -11,7 +11,8 @@
  *   Sect. 3      stopping rule ||x_k - x_{k+1}||_1 <= eps or k >= maxit.
  *
  * Scope: block-tridiagonal Q^T (QBD-like generators) with L levels of m
- * phases each, N = L*m.  Level l (0-based) is block row l+1 of the paper.
+ * phases each, N = L*m, and block-banded Q^T through mc_create_banded.
+ * Level l (0-based) is block row l+1 of the paper.
  *
  * Conventions for every entry point
  *   - Device pointers are CUDA device addresses on the current device; all

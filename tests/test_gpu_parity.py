@@ -305,6 +305,24 @@ def test_paired_pentadiagonal_skips_zero_quadrants(Lp, mp):
     ch.close()
 
 
+def test_paired_chain_in_coupled_mode():
+    """A paired pentadiagonal chain in coupled mode (dense W blocks: the
+    products no longer have zero quadrants, so nothing is skipped) and in
+    STAIR2 order: iterates and solution as the oracle's."""
+    blocks = synth.penta_paired(20, 64, 0.8, 0.3, seed=31)
+    oc = oracle.Chain(*blocks)
+    L, m = 10, 128
+    N = L * m
+    for stair, meth in ((1, oracle.STAIR1), (2, oracle.STAIR2)):
+        ch = mc.Chain(*(dev(b) for b in blocks), paired=True, apply="coupled", stair=stair)
+        x = ch.sweep(torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda"), nsweeps=25)
+        assert rel_l1(x.cpu().numpy(), oc.sweeps(np.full(N, 1.0 / N), 25, method=meth)) <= 1e-12
+        pi, res = ch.solve(tol=1e-12, maxit=200000, check_every=32)
+        sol = oc.solve(tol=1e-13, maxit=200000, check_every=32)["x"]
+        assert res["converged"] and rel_l1(pi.cpu().numpy(), sol) <= 1e-10
+        ch.close()
+
+
 def test_paired_flag_rejects_dense_off_diagonal_blocks():
     blocks = synth.qbd(6, 64, 0.8, seed=3)
     with pytest.raises(mc.McError) as e:
@@ -502,6 +520,29 @@ def test_banded_fused_stats_and_in_place(stair):
             s, d = st.cpu().numpy()[:2]
             assert abs(s - z.sum()) <= 1e-12 * abs(z.sum())
             assert abs(d - np.abs(ref - prev).sum()) <= 1e-12
+    ch.sync()
+    ch.close()
+
+
+def test_banded_sweeps_beyond_one_fused_launch():
+    """Block-banded chain, more sweeps than one fused launch takes: the
+    launches chain through a normalisation and restart their alternating
+    buffers; iterates and stats as the oracle's."""
+    L, m, p, q, K = 14, 8, 1, 3, 1030
+    D = synth.banded(L, m, p, q, 0.8, seed=17)
+    bc = oracle.BandedChain(D)
+    ch = mc.Chain.banded({e: dev(B) for e, B in D.items()})
+    N = L * m
+    x0 = np.random.default_rng(4).random(N)
+    x0 /= x0.sum()
+    st = torch.zeros(3, dtype=torch.float64, device="cuda")
+    x = ch.sweep(dev(x0), nsweeps=K, stats=st)
+    prev = bc.sweeps(x0, K - 1)
+    z = bc.sweep(prev)
+    ref = z / z.sum()
+    assert rel_l1(x.cpu().numpy(), ref) <= 1e-12
+    s, d = st.cpu().numpy()[:2]
+    assert abs(s - z.sum()) <= 1e-12 * abs(z.sum()) and abs(d - np.abs(ref - prev).sum()) <= 1e-12
     ch.sync()
     ch.close()
 

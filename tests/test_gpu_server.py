@@ -45,6 +45,25 @@ def test_server_results_match_oracle(dtype):
 
 
 @pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_server_coupled_stair2_matches_oracle(dtype):
+    """The server in coupled mode with the type-2 stair matrix: each request's
+    pi against the oracle's solution (STAIR2 solve of the same chain)."""
+    srv = mc.Server(2 << 30, dtype=dtype, apply="coupled", stair=2, tol=1e-12, check_every=32,
+                    autotune=False)
+    mix = [(40, 16, 0.6), (64, 64, 0.7), (33, 128, 0.9), (9, 200, 0.85)]
+    for i, (L, m, ratio) in enumerate(mix):
+        assert srv.submit(i, *blocks_for(i, L, m, ratio))
+    res = {t: (pi, r, st) for t, pi, r, st in srv.run_until_idle()}
+    for i, (L, m, ratio) in enumerate(mix):
+        pi, r, st = res[i]
+        assert st == 0 and r["converged"] and r["residual"] <= 1e-12
+        oc = oracle.Chain(*blocks_for(i, L, m, ratio))
+        ref = oc.solve(tol=1e-13, maxit=400000, check_every=64, method=oracle.STAIR2)["x"]
+        assert rel_l1(pi, ref) <= 1e-10, (i, rel_l1(pi, ref))
+    srv.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
 def test_same_result_alone_and_in_the_mix(dtype):
     """A request's iterates do not depend on what else is in the batch, when
     the others arrive, or on the launch grid."""
