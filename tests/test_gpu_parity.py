@@ -96,6 +96,26 @@ def test_one_sweep_from_random_vector():
     ch.close()
 
 
+@pytest.mark.parametrize("stair,apply", [(1, "inverse"), (2, "coupled")])
+def test_gpu_sweep_zeroes_the_coupled_rows_of_the_residual(stair, apply):
+    """Property of the stair splitting (M z = N x row by row, N = 0 on the
+    coupled rows): the GPU iterate after a sweep has Q^T pi = 0 on every
+    coupled block row, to rounding, at a size that spans many warps."""
+    L, m = 200, 48
+    blocks, oc = make(L, m, seed=33)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=stair, apply=apply)
+    x = np.random.default_rng(8).random(L * m)
+    x /= x.sum()
+    for n in (1, 3):
+        pi = ch.sweep(dev(x), nsweeps=n).cpu().numpy()
+        r = oc.residual_vec(pi).reshape(L, m)
+        coupled = np.arange(L) % 2 == (1 if stair == 1 else 0)
+        assert np.abs(r[coupled]).sum() <= 1e-13 * np.abs(r).sum() + 1e-18, n
+        assert np.abs(r[~coupled]).sum() > 0
+    ch.sync()
+    ch.close()
+
+
 def test_residual_parity():
     for (L, m) in [(64, 8), (19, 70), (5, 256)]:
         blocks, oc = make(L, m, seed=L)

@@ -188,6 +188,32 @@ def test_residual_against_dense():
     assert abs(ch.residual(x) - ref) <= 1e-13 * ref
 
 
+@pytest.mark.parametrize("method,coupled_parity", [(oracle.STAIR1, 1), (oracle.STAIR2, 0)])
+def test_stair_sweep_zeroes_the_coupled_rows_of_the_residual(method, coupled_parity):
+    """With M the stair matrix, M z = N x holds row by row; on the coupled
+    (half-sweep-2) block rows M and T agree (N is zero there), so Q^T z = 0
+    on those rows, while on the diagonal-only rows Q^T z = N (x - z)."""
+    L, m = 11, 6
+    dn, loc, up = synth.qbd(L, m, 0.85, seed=12, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    x = np.random.default_rng(3).random(L * m)
+    z = ch.sweep(x, method)
+    r = ch.residual_vec(z).reshape(L, m)
+    scale = np.abs(z).max() * np.abs(dense_QT(dn, loc, up)).max()
+    coupled = np.arange(L) % 2 == coupled_parity
+    assert np.abs(r[coupled]).max() <= 1e-13 * scale
+    # the diagonal-only rows carry the whole residual: N (x - z) there
+    T = dense_QT(dn, loc, up)
+    N = np.zeros_like(T)
+    for l in np.nonzero(~coupled)[0]:
+        s = slice(l * m, (l + 1) * m)
+        N[s] = -T[s]
+        N[s, s] = 0.0
+    ref = (N @ (x - z)).reshape(L, m)
+    assert np.abs(r[~coupled] - ref[~coupled]).max() <= 1e-12 * scale
+    assert np.abs(r[~coupled]).max() > 1e-6 * scale     # not trivially zero
+
+
 # --- LU --------------------------------------------------------------------------
 
 def test_lu_reconstruction_no_swaps_on_diag_blocks():
