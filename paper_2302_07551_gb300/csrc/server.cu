@@ -185,10 +185,20 @@ int retire(mc_server* s, size_t i, int status, double resid, double step, double
 
 // The next chunk (about to run) uses the current counter base; the one after
 // it starts c higher.  Called before each execution of a chunk (a direct
-// enqueue or a graph launch), while no chunk is in flight.
-void begin_chunk(mc_server* s, int c) {
+// enqueue or a graph launch), while no chunk is in flight.  Before the 32-bit
+// counters could wrap, every active request's counters are zeroed (stream
+// ordered before the chunk) and the base restarts at 0.
+int begin_chunk(mc_server* s, int c) {
+  if (s->epoch_next > (1 << 30)) {
+    for (Req* r : s->active)
+      if (cudaMemsetAsync(r->chain->fver, 0, (size_t)r->chain->lay.L * sizeof(int), s->user) !=
+          cudaSuccess)
+        return MC_ERR_CUDA;
+    s->epoch_next = 0;
+  }
   s->t_host->epoch = s->epoch_next;
   s->epoch_next += c;
+  return MC_OK;
 }
 
 // Chunk body on stream st: c fused sweeps (FP64) or one refinement step of c
@@ -444,10 +454,8 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
         const int k = kCand[ci];
         const BGrid gk{k * s->num_sms, 256};
         if (cudaEventRecord(e0, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
-        if (rc == MC_OK) {
-          begin_chunk(s, c);
-          rc = enqueue_chunk(s, gk, c, s->user);
-        }
+        if (rc == MC_OK) rc = begin_chunk(s, c);
+        if (rc == MC_OK) rc = enqueue_chunk(s, gk, c, s->user);
         if (rc == MC_OK && cudaEventRecord(e1, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
         if (rc == MC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = MC_ERR_CUDA;
         float ms = 0.0f;
@@ -490,7 +498,8 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
         s->g_chunk = c;
         s->g_grid = g;
       }
-      begin_chunk(s, c);
+      rc = begin_chunk(s, c);
+      if (rc != MC_OK) return rc;
       if (cudaGraphLaunch(s->gexec, s->user) != cudaSuccess ||
           cudaStreamSynchronize(s->user) != cudaSuccess)
         return MC_ERR_CUDA;
