@@ -81,7 +81,10 @@ __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver
     if (need > 0) wait_neighbours(ver, l, a.L, need, &hdr->status, lane, wait_ns);
     if constexpr (SMALL > 0) {
       using S = typename SmallOf<T>::type;
-      level_sweep_lp_small<S, SMALL, COUPLED, true>(reinterpret_cast<const S*>(a.A),
+      // BF16: 16 loads in flight (single chains; the batched kernel keeps 8,
+      // its register budget buys more resident warps there)
+      constexpr int BW = sizeof(S) == 2 ? 16 : 8;
+      level_sweep_lp_small<S, SMALL, COUPLED, true, BW>(reinterpret_cast<const S*>(a.A),
                                                     reinterpret_cast<const S*>(a.B), a.C, a.sc,
                                                     a.d, a.q, l, a.L, a.m, a.abs_, a.cbs, slice,
                                                     lane);

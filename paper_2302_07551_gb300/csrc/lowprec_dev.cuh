@@ -169,10 +169,10 @@ __device__ __forceinline__ void level_sweep_lp(const T* A, const T* B, const flo
 // per warp load, B loads in flight per lane (at most 64 columns per batch, so
 // v is read inside its 64-float slice); lanes of one row group hold partial
 // sums over different columns until small_combine adds them.
-template <typename S, int ROWS>
+template <typename S, int ROWS, int BW = 8>
 struct SmallLp {
   static constexpr int E = 16 / (int)sizeof(S), LPC = ROWS / E, CPW = 32 / LPC;
-  static constexpr int B = 64 / CPW < 8 ? 64 / CPW : 8;
+  static constexpr int B = 64 / CPW < BW ? 64 / CPW : BW;
 };
 
 __device__ __forceinline__ float small_elem(const uint4& t, int e, float) {
@@ -185,11 +185,11 @@ __device__ __forceinline__ float small_elem(const uint4& t, int e, unsigned shor
 
 // acc[e] += sum over this lane's columns j of M(r0 + e, j) v[j]; v: slice of at
 // least 64 floats, zero beyond m.
-template <typename S, int ROWS>
+template <typename S, int ROWS, int BW = 8>
 __device__ __forceinline__ void gemv_small(float (&acc)[SmallLp<S, ROWS>::E],
                                            const S* __restrict__ M, const float* v, int m,
                                            int lane) {
-  using P = SmallLp<S, ROWS>;
+  using P = SmallLp<S, ROWS, BW>;
   const int c = lane / P::LPC, r0 = P::E * (lane % P::LPC);
   const bool rok = r0 < m;
   for (int jb = 0; jb < m; jb += P::CPW * P::B) {
@@ -220,8 +220,9 @@ __device__ __forceinline__ void small_combine(float (&acc)[SmallLp<S, ROWS>::E])
     for (int e = 0; e < P::E; ++e) acc[e] += __shfl_xor_sync(0xffffffffu, acc[e], o);
 }
 
-// level_sweep_lp for m <= ROWS <= 64 (S as gemv_small; C is FP32).
-template <typename S, int ROWS, bool COUPLED, bool CG = false>
+// level_sweep_lp for m <= ROWS <= 64 (S as gemv_small; C is FP32); BW: loads
+// in flight per lane for the A / B blocks.
+template <typename S, int ROWS, bool COUPLED, bool CG = false, int BW = 8>
 __device__ __forceinline__ void level_sweep_lp_small(const S* A, const S* B, const float* C,
                                                      const float* sc, float* d, const float* q,
                                                      int64_t l, int64_t L, int m, int64_t abs_,
@@ -245,8 +246,8 @@ __device__ __forceinline__ void level_sweep_lp_small(const S* A, const S* B, con
   float acc[E];
 #pragma unroll
   for (int e = 0; e < E; ++e) acc[e] = 0.0f;
-  if (has_lo) gemv_small<S, ROWS>(acc, A + l * abs_, v_lo, m, lane);
-  if (has_up) gemv_small<S, ROWS>(acc, B + l * abs_, v_up, m, lane);
+  if (has_lo) gemv_small<S, ROWS, BW>(acc, A + l * abs_, v_lo, m, lane);
+  if (has_up) gemv_small<S, ROWS, BW>(acc, B + l * abs_, v_up, m, lane);
   small_combine<S, ROWS>(acc);
   const int r0 = E * (lane % LPC);
   const bool writer = lane < LPC && r0 < m;   // one lane per row group
