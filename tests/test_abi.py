@@ -85,3 +85,14 @@ def test_status_strings(lib):
     for s in range(0, 9):
         assert lib.mc_status_string(s).decode() not in ("", "unknown status")
     assert lib.mc_status_string(99).decode() == "unknown status"
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without libmc.so the binding raises: there is no CPU fallback."""
+    monkeypatch.setattr(nat, "LIB_PATH", "/nonexistent/libmc.so")
+    monkeypatch.setattr(nat, "_lib", None)
+    with pytest.raises(ImportError):
+        nat.load()
+    import paper_2302_07551_gb300 as mc
+    with pytest.raises(ImportError):
+        mc.Chain.__init__(object.__new__(mc.Chain), *([None] * 3))
