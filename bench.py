@@ -411,7 +411,7 @@ def run_solve(args):
     # paired pentadiagonal workloads: the FP64 inverse-mode form skips the
     # structurally zero quadrants (as in the throughput line)
     penta = synth.WORKLOADS[name]["kind"] == "penta" and m % 64 == 0
-    for dtype in ("f64", "f32", "bf16"):
+    for dtype in args.solve_dtypes.split(","):
         paired = penta and dtype == "f64" and args.apply == "inverse"
         ch = mcl.Chain(*d, apply=args.apply, dtype=dtype, paired=paired)
         torch.cuda.synchronize()
@@ -420,11 +420,12 @@ def run_solve(args):
         torch.cuda.synchronize()
         t = time.perf_counter() - t0
         p = pi.cpu().numpy()
-        if ref is None:
+        if ref is None and dtype == "f64":
             ref = p
         rows.append({"dtype": dtype, "paired": paired, "seconds": t, "sweeps": res["sweeps"],
                      "residual": res["residual"], "converged": res["converged"],
-                     "rel_l1_vs_f64": float(np.abs(p - ref).sum() / np.abs(ref).sum()),
+                     "rel_l1_vs_f64": (float(np.abs(p - ref).sum() / np.abs(ref).sum())
+                                       if ref is not None else None),
                      "ms_per_sweep": 1e3 * t / max(res["sweeps"], 1)})
         ch.close()
     print(json.dumps({"mode": "time_to_solution", "workload": name, "L": L, "m": m,
@@ -614,6 +615,8 @@ def main():
     ap.add_argument("--solve", action="store_true",
                     help="time one full solve to --tol per dtype instead of sweeps")
     ap.add_argument("--tol", type=float, default=1e-12)
+    ap.add_argument("--solve-dtypes", default="f64,f32,bf16",
+                    help="comma list of storage types for --solve (f64 first for the distances)")
     ap.add_argument("--serve", action="store_true", help="serving benchmark on the request stream")
     ap.add_argument("--contraction", action="store_true",
                     help="contraction factors of stair / block Jacobi / block Gauss-Seidel")
