@@ -90,3 +90,30 @@ def test_reference_arm_line_on_rank0(monkeypatch, capsys):
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
     assert line["config"]["workload"] == "qbd_L64_m8"
+
+
+def test_clock_sampler_reports_median_clock_and_throttle_reasons(tmp_path, monkeypatch):
+    """The clock record of the bench line: median SM clock under load, the
+    maximum, and every throttle reason that was active in any sample (a fake
+    nvidia-smi on PATH stands in for the GPU machine's)."""
+    import time
+    sys.path.insert(0, ROOT)
+    import bench
+    fake = tmp_path / "nvidia-smi"
+    fake.write_text("#!/bin/sh\n"
+                    "echo '2070, 2070, 500.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "echo '1980, 2070, 610.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
+                    "echo '2070, 2070, 590.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
+                    "exec sleep 30\n")
+    fake.chmod(0o755)
+    monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ.get('PATH', '')}")
+    s = bench.ClockSampler(0)
+    s.start()
+    for _ in range(100):
+        if len(s.rows) >= 3:
+            break
+        time.sleep(0.05)
+    out = s.stop()
+    assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
+    assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
+    assert out["power_w_max"] == 610.5
