@@ -39,10 +39,33 @@ def peaks():
 
 
 # FP64 peak of a GB300: 152 SMs x 2 DFMA/clk/SM x 2 flop x 2.07 GHz (maximum
-# SM clock) = 1.2586 TFLOP/s.  The 2 DFMA/clk/SM rate is measured: a loop of
-# independent DFMA chains reaches 1.195 TFLOP/s and cuBLAS DGEMM 1.100 TFLOP/s
-# at 2070 MHz (profiles/fp64_peak.md).
+# SM clock) = 1.2586 TFLOP/s.  The 2 DFMA lanes/clk/SM pipe rate is what
+# ncu's FP64-pipe utilisation of the sweep kernel implies (95 % busy at
+# 1.215 TFLOP/s); the independent FMA-loop probe (--measure-fp64-peak) and
+# cuBLAS DGEMM are reported beside it.
 FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.07e9 / 1e12
+
+
+def gpu_id(local):
+    """nvidia-smi selector of the CUDA device `local` of this process.
+
+    nvidia-smi numbers GPUs in its own (PCI) order and ignores
+    CUDA_VISIBLE_DEVICES, so a CUDA ordinal is not an nvidia-smi index: the
+    device is named by its UUID (from torch, else from a UUID entry of
+    CUDA_VISIBLE_DEVICES); an index is used only when neither is known."""
+    try:
+        import torch
+        u = str(torch.cuda.get_device_properties(local).uuid)
+        if u and u != "None":
+            return u if u.startswith(("GPU-", "MIG-")) else "GPU-" + u
+    except Exception:
+        pass
+    vis = [v.strip() for v in os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",") if v.strip()]
+    if local < len(vis) and vis[local].startswith(("GPU-", "MIG-")):
+        return vis[local]
+    if local < len(vis) and vis[local].isdigit():
+        return vis[local]
+    return str(local)
 
 
 class ClockSampler:
@@ -52,15 +75,15 @@ class ClockSampler:
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
          "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
 
-    def __init__(self, index):
-        self.index = index
+    def __init__(self, gpu):
+        self.gpu = str(gpu)       # nvidia-smi selector: UUID (gpu_id) or index
         self.rows = []
         self.proc = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
-                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                ["nvidia-smi", "-i", self.gpu, f"--query-gpu={self.Q}",
                  "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except OSError:
@@ -77,7 +100,8 @@ class ClockSampler:
 
     def stop(self):
         if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"],
+                    "gpu": self.gpu}
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
@@ -92,7 +116,8 @@ class ClockSampler:
         pw = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
         return {"sm_mhz": statistics.median(sm) if sm else None,
                 "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
-                "samples": len(self.rows), "power_w_max": max(pw) if pw else None}
+                "samples": len(self.rows), "power_w_max": max(pw) if pw else None,
+                "gpu": self.gpu}
 
 
 def dist_env():
@@ -239,7 +264,7 @@ def run_mine(args):
     x = torch.full((N,), 1.0 / N, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
     torch.cuda.synchronize()
-    sampler = ClockSampler(local)
+    sampler = ClockSampler(gpu_id(local))
     sampler.start()
     time.sleep(0.3)
     for _ in range(args.warmup):
@@ -352,7 +377,7 @@ def run_mine(args):
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic,
                 "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps per launch)",
-                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz (the pipe rate from ncu's FP64-pipe utilisation of this kernel, profiles/fp64_peak.md)",
+                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz (the pipe rate implied by ncu's FP64-pipe utilisation of this kernel)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
@@ -550,42 +575,56 @@ def run_contraction(args):
 
 
 def measure_fp64_peak():
-    """FP64 multiply-add peak of this GPU: an fma-loop kernel of the library
-    (mc_fp64_rate: 8 independent chains per thread, 1-8 blocks of 128-512
-    threads per SM, best of the grid shapes) and cuBLAS DGEMM 8192^3 (best of
-    10), with the SM clock sampled meanwhile; the per-SM rate follows from the
-    loop's TFLOP/s, the SM count and the median SM clock."""
+    """FP64 multiply-add peak of this GPU: the probe library's fma loop
+    (libmcprobe.so: 8, 16 or 32 independent chains per thread, unrolled 4x,
+    1-8 blocks of 128-1024 threads per SM, best of the grid shapes) and cuBLAS
+    DGEMM 8192^3 (best of 10), with the SM clock sampled meanwhile; the per-SM
+    rate follows from the loop's TFLOP/s, the SM count and the median SM
+    clock."""
     import ctypes
 
     import torch
 
-    from paper_2302_07551_gb300 import _native as nat
+    from paper_2302_07551_gb300 import build as pbuild
     torch.cuda.set_device(0)
     sms = torch.cuda.get_device_properties(0).multi_processor_count
-    lib = nat.load()
+    if not os.path.exists(pbuild.PROBE_LIB):
+        raise RuntimeError(f"{pbuild.PROBE_LIB} not built; run __graft_entry__.build()")
+    lib = ctypes.CDLL(pbuild.PROBE_LIB)
+    lib.mcprobe_fp64_rate.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int64, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_double)]
+    lib.mcprobe_fp64_rate.restype = ctypes.c_int
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
     loop = []
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(gpu_id(0))
     sampler.start()
-    for reg in (1, 0):
-        for per_sm in (1, 2, 4, 8):
-            for threads in (128, 256, 512):
-                v = ctypes.c_double(0.0)
-                nat.check(lib.mc_fp64_rate(stream, per_sm * sms, threads, 1 << 16, reg,
-                                           ctypes.byref(v)), "mc_fp64_rate")
-                loop.append({"blocks": per_sm * sms, "threads": threads, "reg_operands": reg,
-                             "tflops": v.value})
+    for chains in (8, 16, 32):
+        for reg in (1, 0):
+            for per_sm in (1, 2, 4, 8):
+                for threads in (128, 256, 512, 1024):
+                    v = ctypes.c_double(0.0)
+                    iters = (1 << 18) // chains
+                    rc = lib.mcprobe_fp64_rate(stream, per_sm * sms, threads, iters, chains, reg,
+                                               ctypes.byref(v))
+                    if rc == 1:        # block too large for this variant's registers
+                        continue
+                    if rc != 0:
+                        raise RuntimeError(f"mcprobe_fp64_rate failed ({rc})")
+                    loop.append({"chains": chains, "blocks": per_sm * sms, "threads": threads,
+                                 "reg_operands": reg, "tflops": v.value})
     loop_clocks = sampler.stop()
-    best_loop = max(r["tflops"] for r in loop)
+    best = max(loop, key=lambda r: r["tflops"])
+    best_loop = best["tflops"]
     mhz = loop_clocks.get("sm_mhz") or 0.0
     n = 8192
     a = torch.rand(n, n, dtype=torch.float64, device="cuda")
     b = torch.rand(n, n, dtype=torch.float64, device="cuda")
     c = a @ b
     torch.cuda.synchronize()
-    sampler = ClockSampler(0)
+    sampler = ClockSampler(gpu_id(0))
     sampler.start()
-    best = 0.0
+    dgemm = 0.0
     for _ in range(10):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -593,12 +632,13 @@ def measure_fp64_peak():
         c = a @ b
         e1.record()
         torch.cuda.synchronize()
-        best = max(best, 2 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
+        dgemm = max(dgemm, 2 * n ** 3 / (e0.elapsed_time(e1) * 1e-3) / 1e12)
     clocks = sampler.stop()
     per_sm_clk = best_loop * 1e12 / (2 * sms * mhz * 1e6) if mhz else None
-    print(json.dumps({"fp64_fma_loop_tflops": best_loop, "fma_loop_clocks": loop_clocks,
-                      "sms": sms, "dfma_lanes_per_clk_per_sm": per_sm_clk,
-                      "fp64_dgemm_tflops": best, "n": n, "clocks": clocks,
+    print(json.dumps({"fp64_fma_loop_tflops": best_loop, "best_shape": best,
+                      "fma_loop_clocks": loop_clocks, "sms": sms,
+                      "dfma_lanes_per_clk_per_sm": per_sm_clk,
+                      "fp64_dgemm_tflops": dgemm, "n": n, "clocks": clocks,
                       "fma_loop_grid": loop}), flush=True)
 
 

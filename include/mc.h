@@ -218,19 +218,6 @@ int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, 
 int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns);
 
 /*
- * FP64 multiply-add rate of the current GPU (a diagnostic for the roofline
- * denominator; no counterpart in the paper): `blocks` blocks of `threads`
- * threads (a multiple of 32, at most 1024; 1 <= blocks <= 8192) each run 8
- * independent fma chains for `iters` steps (1 <= iters <= 2^32), with the
- * multipliers and the addend in registers loaded from memory (reg != 0) or
- * taken from the kernel parameters (reg == 0); *tflops receives
- * 2 * 8 * iters * threads * blocks / (event time) in TFLOP/s.  Uses small
- * static device buffers.  Syncs cuda_stream.  Errors: MC_ERR_ARG, MC_ERR_CUDA.
- */
-int mc_fp64_rate(void* cuda_stream, int blocks, int threads, int64_t iters, int reg,
-                 double* tflops);
-
-/*
  * Diagnostics: for FP64 chains exactly mc_sweep(x_in, x_out, nsweeps, NULL);
  * for low-precision chains (MC_F32 / MC_BF16) the correction sweeps of one
  * refinement step from x_in (r and q of x_in, then nsweeps correction sweeps

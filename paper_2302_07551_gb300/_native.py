@@ -73,8 +73,6 @@ def load():
     lib.mc_residual_noalloc.restype = ctypes.c_int
     lib.mc_wait_selftest.argtypes = [vp, i32, i64]
     lib.mc_wait_selftest.restype = ctypes.c_int
-    lib.mc_fp64_rate.argtypes = [vp, i32, i32, i64, i32, ctypes.POINTER(dbl)]
-    lib.mc_fp64_rate.restype = ctypes.c_int
     lib.mc_server_create.argtypes = [ctypes.POINTER(McServerDesc), vp, sz, vp, ctypes.POINTER(vp)]
     lib.mc_server_create.restype = ctypes.c_int
     lib.mc_server_request_bytes.argtypes = [vp, i64, i32]

@@ -10,6 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libmc.so")
+# the benchmark's FP64-rate probe: a separate library, not part of libmc's ABI
+PROBE_SRC = os.path.join(HERE, "probe", "fp64_rate.cu")
+PROBE_LIB = os.path.join(HERE, "libmcprobe.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]
@@ -36,11 +39,14 @@ def up_to_date():
 
 
 def build(force=False, verbose=False, extra=()):
-    """Compile every .cu under csrc/ and link libmc.so next to this file."""
+    """Compile every .cu under csrc/ and link libmc.so next to this file (and
+    the benchmark's probe library libmcprobe.so beside it)."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     cc = nvcc()
+    probe = subprocess.Popen([cc, *ARCH, *FLAGS, "-shared", "-o", PROBE_LIB + ".tmp", PROBE_SRC],
+                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT, text=True)
 
     def one(src):
         obj = os.path.join(BUILD, os.path.basename(src) + ".o")
@@ -62,6 +68,10 @@ def build(force=False, verbose=False, extra=()):
         print(" ".join(cmd), flush=True)
     subprocess.check_call(cmd)
     os.replace(tmp, LIB)
+    out, _ = probe.communicate()
+    if probe.returncode != 0:
+        raise RuntimeError(f"nvcc failed on {PROBE_SRC}:\n{out}")
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
     return LIB
 
 

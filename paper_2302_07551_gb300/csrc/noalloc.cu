@@ -12,8 +12,9 @@
 //
 // Scratch contents: one |.|-sum per level (so at most kNoAllocMaxLevels
 // levels) and one ticket counter for the last-block-done reduction.  The
-// ticket is cleared by a memset at the start of every call; the per-level
-// slots are all overwritten before they are read.  Calls share the array, so
+// ticket is cleared only by a memset enqueued at the start of every call
+// (which also recovers from an earlier launch that did not finish); the
+// per-level slots are all overwritten before they are read.  Calls share the array, so
 // two calls whose kernels overlap on the GPU (different streams, or different
 // host threads) race and must be serialised by the caller.
 //
@@ -82,7 +83,9 @@ __device__ __forceinline__ void vec_na(double (&v)[R], const double* __restrict_
 
 // One warp per level: level_sum[l] = || (Q^T pi)_l ||_1 with
 // (Q^T pi)_l = up[l-1]^T pi_{l-1} + loc[l]^T pi_l + dn[l+1]^T pi_{l+1};
-// the last block sums level_sum[0..L) in level order into *out.
+// the last block adds level_sum[0..L) into *out in a fixed order (per-thread
+// strided partial sums, then a warp and block shuffle tree), which is
+// deterministic for the 256-thread block.
 template <int R>
 __global__ void __launch_bounds__(256) k_residual_noalloc(const double* __restrict__ dn,
                                                           const double* __restrict__ loc,
@@ -133,10 +136,7 @@ __global__ void __launch_bounds__(256) k_residual_noalloc(const double* __restri
   if (threadIdx.x < 32) {
     double u = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
     u = warp_sum_na(u);
-    if (threadIdx.x == 0) {
-      *out = u;
-      sc->ticket = 0u;
-    }
+    if (threadIdx.x == 0) *out = u;
   }
 }
 

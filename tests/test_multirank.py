@@ -100,14 +100,21 @@ def test_clock_sampler_reports_median_clock_and_throttle_reasons(tmp_path, monke
     sys.path.insert(0, ROOT)
     import bench
     fake = tmp_path / "nvidia-smi"
+    argf = tmp_path / "args"
     fake.write_text("#!/bin/sh\n"
+                    f"echo \"$@\" > {argf}\n"
                     "echo '2070, 2070, 500.1, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
                     "echo '1980, 2070, 610.5, 0x4, Not Active, Not Active, Not Active, Active'\n"
                     "echo '2070, 2070, 590.0, 0x0, Not Active, Not Active, Not Active, Not Active'\n"
                     "exec sleep 30\n")
     fake.chmod(0o755)
     monkeypatch.setenv("PATH", f"{tmp_path}:{os.environ.get('PATH', '')}")
-    s = bench.ClockSampler(0)
+    # the timed GPU is named by UUID: nvidia-smi's own indices ignore
+    # CUDA_VISIBLE_DEVICES, so ordinal 0 of this process may be another GPU
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "GPU-1234abcd-0000-1111-2222-333344445555")
+    sel = bench.gpu_id(0)
+    assert sel == "GPU-1234abcd-0000-1111-2222-333344445555"
+    s = bench.ClockSampler(sel)
     s.start()
     for _ in range(100):
         if len(s.rows) >= 3:
@@ -117,3 +124,7 @@ def test_clock_sampler_reports_median_clock_and_throttle_reasons(tmp_path, monke
     assert out["sm_mhz"] == 2070.0 and out["sm_max_mhz"] == 2070.0
     assert out["reasons"] == ["sw_power_cap"] and out["samples"] == 3
     assert out["power_w_max"] == 610.5
+    assert out["gpu"] == sel
+    assert argf.read_text().split()[:2] == ["-i", sel]
+    monkeypatch.setenv("CUDA_VISIBLE_DEVICES", "3,5")
+    assert bench.gpu_id(1) == "5"

@@ -145,6 +145,33 @@ def test_sweeps_equal_dense_splittings(L, m):
         assert np.abs(z - ref).max() <= 1e-12 * np.abs(ref).max(), meth
 
 
+@pytest.mark.parametrize("L,m", [(7, 3), (11, 6)])
+@pytest.mark.parametrize("meth", [oracle.STAIR1, oracle.STAIR2, oracle.BGS, oracle.BJ])
+def test_normalised_sweep_equals_dense_step(L, m, meth):
+    """One step of Eq. (2) (the expected [e^T z, step] of every GPU stats
+    check): z = M^{-1} N x from independently assembled M and N, s = e^T z,
+    pi = z / s, and the step error ||pi - x||_1 against the normalised pi.
+    x is a unit-L1 vector far from equilibrium, so s differs from 1 and a
+    step error taken against the unnormalised z, or s summed over x, fails."""
+    dn, loc, up = synth.qbd(L, m, 0.8, seed=50 + L * m, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    T = dense_QT(dn, loc, up)
+    M = {oracle.STAIR1: stair_M(T, L, m, 1), oracle.STAIR2: stair_M(T, L, m, 2),
+         oracle.BGS: bgs_M(T, L, m), oracle.BJ: bj_M(T, L, m)}[meth]
+    x = np.random.default_rng(L + 7 * m).random(L * m) ** 4
+    x /= x.sum()
+    z = np.linalg.solve(M, (M - T) @ x)
+    s_ref = z.sum()
+    pi_ref = z / s_ref
+    d_ref = np.abs(pi_ref - x).sum()
+    pi, s, d = ch.normalised_sweep(x, meth)
+    assert abs(s - s_ref) <= 1e-14 * abs(s_ref)
+    assert np.abs(pi - pi_ref).sum() <= 1e-14 * np.abs(pi_ref).sum()
+    assert abs(d - d_ref) <= 1e-14
+    assert abs(s_ref - 1.0) > 1e-3 and abs(np.abs(z - x).sum() - d_ref) > 1e-6
+    assert abs(x.sum() - s_ref) > 1e-3
+
+
 @pytest.mark.parametrize("L,m", [(7, 3), (8, 4), (5, 1)])
 def test_sweep_with_rhs_equals_dense(L, m):
     """The refinement step z = M^{-1}(N x + b), against dense M and N."""
