@@ -274,16 +274,34 @@ def run_mine(args):
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    # timed region: K sweeps, CUDA events on the chain's stream around each
-    # kernel launch (mc_profile) and around the whole region
+    # timed region: K sweeps as the solve loop runs them -- chunks of
+    # --check-every sweeps, each one fused launch that ends with the residual
+    # of its result (formed from the splitting), the scale reduction and the
+    # normalisation, then a host read of [e^T z, step, residual] (the stopping
+    # test); CUDA events on the chain's stream around the whole region
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
+    check = max(1, args.refine_every)
+    resid_checks = []
     if args.dtype == "f64":
+        st = torch.zeros(3, dtype=torch.float64, device=dev)
+        sth = torch.zeros(3, dtype=torch.float64).pin_memory()
         e0.record(stream)
-        _, prof = ch.profile(x, y, args.steps)
+        with torch.cuda.stream(stream):
+            for done in range(0, args.steps, check):
+                ch.sweep(x, x, min(check, args.steps - done), stats=st)
+                sth.copy_(st, non_blocking=True)
+                stream.synchronize()
+                resid_checks.append(float(sth[2]))
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1)
+        # per-kernel device times of one launch of the same size (at most 1024
+        # sweeps per fused launch) with its residual units
+        prof_steps = min(args.steps, check, 1024)
+        _, prof = ch.profile(x, y, prof_steps)
+        torch.cuda.synchronize()
+        x, y = y, x
     else:
         # a step = one correction sweep of mixed-precision refinement, with the
         # FP64 outer step (residual, q, update, renormalisation) every
@@ -300,7 +318,9 @@ def run_mine(args):
         torch.distributed.barrier()
     x, y = y, x
 
-    # end to end through host buffers (pinned), copies inside the timed region
+    # end to end through host buffers (pinned): every step one mc_sweep_host
+    # call, which reads x from pinned host memory and returns pi there; the
+    # stats with the residual every --check-every steps, as the solve loop
     xh = torch.empty(N, dtype=torch.float64).pin_memory()
     yh = torch.empty(N, dtype=torch.float64).pin_memory()
     xh.copy_(x.cpu())
@@ -308,8 +328,8 @@ def run_mine(args):
     ch.sweep_host(xh, yh, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    for _ in range(ke):
-        ch.sweep_host(xh, yh, 1)
+    for i in range(ke):
+        ch.sweep_host(xh, yh, 1, stats=(i % check == check - 1 or i == ke - 1))
         xh, yh = yh, xh
     e2e_s = time.perf_counter() - t0
     clocks = sampler.stop()
@@ -322,12 +342,20 @@ def run_mine(args):
     nmat = 3 if args.apply == "inverse" else 2
     if banded:
         nmat = n_diags       # every off-diagonal block of Q^T plus (-T_dd)^{-1}
+    tail_bytes = tail_flops = 0
     if args.dtype == "f64":
         # paired chains stream 3/4 of each off-diagonal block
         mats = (2.5 if paired else nmat)
         bytes_level = int(8 * mats * m * m) + 16 * m
         sweep_bytes = L * int(8 * mats * m * m) + 16 * N
-        prof_steps = args.steps
+        if not banded:
+            # residual units of the last launch: T_lo and T_up of every
+            # diagonal-only level (3/4 of each when paired) and z_K, z_{K-1}
+            # at its two neighbours
+            offd = 1.5 if paired else 2.0
+            p0 = (L + 1) // 2
+            tail_bytes = p0 * (int(8 * offd * m * m) + 32 * m)
+            tail_flops = p0 * int(2 * offd * m * m)
     else:
         # FP32 vectors: neighbour d read, q read, d written (16 m bytes / level)
         es = 4 if args.dtype == "f32" else 2
@@ -340,9 +368,16 @@ def run_mine(args):
     fused = prof["fused"]
     sweeps_per_launch = min(prof_steps, 1024) if fused else 1
     n_launch = -(-prof_steps // sweeps_per_launch)
+    # kernels of this library launched inside the timed region: per chunk the
+    # fused sweeps (+ residual units), the scale reduction and the
+    # normalisation; mixed precision: the start (scale check, residual with
+    # q) and per refinement step the fused correction sweeps, the update, the
+    # normalisation and the residual with q
+    n_chunks = -(-args.steps // check)
+    n_kernels = 3 * n_chunks if args.dtype == "f64" else 2 + 4 * n_chunks
     kern_ms = prof["sweeps_ms"] / n_launch
-    kern_bytes = bytes_level * L * sweeps_per_launch
-    kern_flops = flops_level * L * sweeps_per_launch
+    kern_bytes = bytes_level * L * sweeps_per_launch + tail_bytes
+    kern_flops = flops_level * L * sweeps_per_launch + tail_flops
     kern_ms_per_sweep = {"sweeps": prof["sweeps_ms"] / prof_steps,
                          "scale": prof["scale_ms"] / prof_steps,
                          "normalise": prof["norm_ms"] / prof_steps}
@@ -376,7 +411,7 @@ def run_mine(args):
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic,
-                "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps per launch)",
+                "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps + residual units per launch)",
                 "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz (the pipe rate implied by ncu's FP64-pipe utilisation of this kernel)",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
@@ -392,6 +427,7 @@ def run_mine(args):
         "dtype": "f64" if args.dtype == "f64" else f"{args.dtype} blocks, f32 sweeps, f64 refinement",
         "data": "synthetic (seeded QBD generator, level-dependent blocks)",
         "config": {"workload": name, "L": L, "m": m, "N": N, "apply": args.apply, "stair": 1,
+                   "check_every": check if args.dtype == "f64" else None,
                    "paired_zero_quadrants_skipped": bool(paired),
                    "block_bytes": sweep_bytes - 16 * N,
                    "refine_every": args.refine_every if args.dtype != "f64" else None,
@@ -400,9 +436,12 @@ def run_mine(args):
         "gbs_per_sweep": sweep_bytes / (ms / args.steps * 1e-3) / 1e9,
         "roofline": roof,
         "kernel_ms_per_sweep": kern_ms_per_sweep,
+        "residual_checks": resid_checks[-3:],
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 8 * N,
-                "d2h_bytes_per_step": 8 * N + 8 * 3},
-        "gpu_launches": prof["launches"],
+                "d2h_bytes_per_step": 8 * N + 8 * 3,
+                "how": "mc_sweep_host per step: x read from pinned host memory by the "
+                       "kernels, pi stored into pinned host memory by the normalisation"},
+        "gpu_launches": n_kernels,
         "clocks": clocks,
         "setup_s": setup_s,
         "cpu_baseline": cpu,
@@ -651,7 +690,8 @@ def main():
     ap.add_argument("--workload", default="qbd_L32768_m64")
     ap.add_argument("--apply", default="inverse", choices=["inverse", "coupled"])
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "bf16"])
-    ap.add_argument("--refine-every", type=int, default=64)
+    ap.add_argument("--refine-every", "--check-every", dest="refine_every", type=int, default=64,
+                    help="sweeps per residual check (FP64) / correction sweeps per refinement step")
     ap.add_argument("--solve", action="store_true",
                     help="time one full solve to --tol per dtype instead of sweeps")
     ap.add_argument("--tol", type=float, default=1e-12)

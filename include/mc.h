@@ -178,7 +178,15 @@ int mc_factor(mc_chain* chain);
  *     for step to be the paper's step error.
  *   nsweeps >= 1.
  *   stats_dev: NULL or device array of 3 doubles receiving, for the last
- *     sweep, [e^T z, ||x_new - x_old||_1, NaN] (the third slot is reserved).
+ *     sweep, [e^T z, ||x_new - x_old||_1, ||Q^T x_out||_1].  The residual
+ *     (Eq. (1)) of a block-tridiagonal stair chain comes from the splitting:
+ *     the last sweep solved M z = N x, so Q^T z = N (x - z), which is zero on
+ *     the coupled block rows and T_lo d_{l-1} + T_up d_{l+1} (d = z - x) on
+ *     the diagonal-only rows; it costs one pass over the two off-diagonal
+ *     blocks of half the levels (a third of a sweep's bytes in inverse mode)
+ *     at the end of the last fused launch.  Other chains (block-banded,
+ *     block Jacobi / Gauss-Seidel) compute the direct residual.  With
+ *     stats_dev == NULL no residual is formed.
  * Block-tridiagonal chains with a stair splitting (desc.stair 1 or 2) run the
  * nsweeps sweeps as one persistent launch per 1024 sweeps, with no
  * normalisation between the sweeps of a launch (the scale of the iterate
@@ -195,12 +203,14 @@ int mc_sweep(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps
              double* stats_dev);
 
 /*
- * As mc_sweep but with HOST vectors (pinned memory recommended): copies
- * x_in_host to the device, sweeps, and returns the result in x_out_host and
- * stats (3 doubles, may be NULL) in stats_host.  When x_out_host is
- * page-locked (cudaHostAlloc / cudaHostRegister) and the sweeps run as one
- * fused launch, the normalisation stores the result into it directly;
- * otherwise the result is copied back.  Syncs.
+ * As mc_sweep but with HOST vectors (pinned memory recommended): returns the
+ * result in x_out_host and the stats of mc_sweep (3 doubles, residual
+ * included; NULL: no stats and no residual) in stats_host.  Stair chains
+ * read a page-locked x_in_host (cudaHostAlloc / cudaHostRegister) in place
+ * from the kernels over the CPU-GPU link, and when x_out_host is page-locked
+ * and the sweeps run as one fused launch, the normalisation stores the
+ * result into it directly; pageable buffers are copied.  x_in_host may equal
+ * x_out_host.  Syncs.
  */
 int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, int64_t nsweeps,
                   double* stats_host);
@@ -218,7 +228,10 @@ int mc_sweep_host(mc_chain* chain, const double* x_in_host, double* x_out_host, 
 int mc_wait_selftest(void* cuda_stream, int reachable, int64_t wait_ns);
 
 /*
- * Diagnostics: for FP64 chains exactly mc_sweep(x_in, x_out, nsweeps, NULL);
+ * Diagnostics: for FP64 chains exactly mc_sweep(x_in, x_out, nsweeps, stats)
+ * with the stats kept in the handle (block-tridiagonal stair chains form the
+ * residual from the splitting at the end of the last fused launch, as one
+ * chunk of mc_solve does);
  * for low-precision chains (MC_F32 / MC_BF16) the correction sweeps of one
  * refinement step from x_in (r and q of x_in, then nsweeps correction sweeps
  * from d = 0 in one fused launch; x_out = x_in).  CUDA events are recorded on
@@ -240,8 +253,14 @@ int mc_profile(mc_chain* chain, const double* x_in, double* x_out, int64_t nswee
  *   x0: NULL (start from the uniform vector 1/N) or a device vector of N
  *     doubles, entries >= 0 with positive sum (normalised on entry).
  *   pi: device output, N doubles.
- *   tol: stop when ||Q^T pi||_1 <= tol (direct FP64 residual, evaluated every
- *     check_every sweeps and at maxit); tol <= 0 disables.
+ *   tol: stop when ||Q^T pi||_1 <= tol, evaluated every check_every sweeps
+ *     and at maxit; tol <= 0 disables.  Block-tridiagonal stair chains take
+ *     the residual from the splitting inside the chunk's last fused launch
+ *     (see mc_sweep) and confirm it with the direct FP64 residual before
+ *     stopping (if the direct one is still above tol, rounding near the
+ *     floor, the iteration continues); other chains evaluate the direct
+ *     residual every check.  res->residual_l1 is always the direct residual
+ *     of the returned pi.
  *   eps: stop when the step error of Sect. 3 is <= eps (evaluated every
  *     check_every sweeps); eps <= 0 disables.
  *   maxit: sweep limit (>= 1).  check_every >= 1: sweeps per check; the

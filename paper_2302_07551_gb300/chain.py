@@ -105,15 +105,17 @@ class Chain:
         return x_out, dict(fused=ms[4] == 1.0, sweeps_ms=ms[0], scale_ms=ms[1], norm_ms=ms[2],
                            launches=int(ms[3]))
 
-    def sweep_host(self, x_in, x_out, nsweeps=1):
-        """Host-buffer variant (x_in, x_out: CPU float64, ideally pinned)."""
+    def sweep_host(self, x_in, x_out, nsweeps=1, stats=True):
+        """Host-buffer variant (x_in, x_out: CPU float64, ideally pinned).
+        Returns [e^T z, step, residual] (stats=True) or None (stats=False:
+        no residual is formed)."""
         for t in (x_in, x_out):
             if t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous() or t.numel() != self.N:
                 raise ValueError("host vectors must be contiguous float64 CPU tensors of length N")
-        st = (ctypes.c_double * 3)()
+        st = (ctypes.c_double * 3)() if stats else None
         nat.check(self._lib.mc_sweep_host(self._h, _ptr(x_in), _ptr(x_out), int(nsweeps), st),
                   "mc_sweep_host")
-        return list(st)
+        return list(st) if stats else None
 
     def solve(self, x0=None, tol=1e-12, eps=0.0, maxit=1_000_000, check_every=32, pi=None,
               raise_on_maxit=True):

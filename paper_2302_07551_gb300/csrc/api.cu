@@ -59,7 +59,8 @@ Layout make_layout(const mc_desc& d) {
   y.off_rpart = o;
   o += round_up(kMaxWarps * sizeof(double), 256);
   y.off_fsum = o;
-  o += round_up((2 * (size_t)d.L + 2 + 2 * kScaleBlocks) * sizeof(double), 256);
+  // [2][L] level sums of e^T z, [L] residual sums, 4 scale slots, partials
+  o += round_up((3 * (size_t)d.L + 4 + 3 * kScaleBlocks) * sizeof(double), 256);
   y.off_fver = o;
   o += round_up(sizeof(unsigned long long) + (size_t)d.L * sizeof(int), 256);
   y.lp = d.dtype == MC_F32 ? 1 : d.dtype == MC_BF16 ? 2 : 0;
@@ -158,18 +159,26 @@ constexpr unsigned long long kFusedWaitNs = 2000000000ull;
 // alternating buffers); block Jacobi / Gauss-Seidel one sweep at a time.
 static bool fused_ok(const mc_chain* c) { return c->d.stair <= 2; }
 
+// Block-tridiagonal stair splittings get the residual of a fused launch's
+// result from the splitting (residual units at the end of the launch); other
+// chains use the direct residual.
+static bool split_resid_ok(const mc_chain* c) { return fused_ok(c) && c->lay.nfar == 0; }
+
 // n stair sweeps src -> dst (in place allowed) as fused launches of at most
 // kMaxFusedSweeps sweeps, each followed by the normalisation (with the step
-// error after the last).  ev (optional, 4 events): before the first launch,
-// after the last fused kernel, after its scale reduction, after the last
-// normalisation.
+// error after the last).  With resid (block-tridiagonal chains only) the last
+// launch also forms ||Q^T dst||_1 from the splitting into stats[2].  ev
+// (optional, 4 events): before the first launch, after the last fused kernel,
+// after its scale reduction, after the last normalisation.
 static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int64_t n,
-                                double* stats_out, cudaStream_t s, cudaEvent_t* ev) {
+                                double* stats_out, cudaStream_t s, cudaEvent_t* ev,
+                                bool resid) {
   const bool coupled = c->d.apply == MC_APPLY_COUPLED;
   const size_t pe = c->lay.plane_bytes / sizeof(double);
   const int64_t L = c->lay.L;
   const size_t cnt_bytes = sizeof(unsigned long long) + (size_t)L * sizeof(int);
-  double* scale = c->flsum + 2 * L;
+  double* rsum = c->flsum + 2 * L;
+  double* scale = c->flsum + 3 * L;
   const bool banded = c->lay.nfar > 0;
   int bw = 1;
   for (int i = 0; i < c->lay.nfar; ++i) {
@@ -202,12 +211,22 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     a.wait_ns = kFusedWaitNs;
     a.far = banded ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
     a.bw = bw;
+    const bool with_resid = resid && final && !banded;
+    if (with_resid) {
+      a.with_resid = 1;
+      a.RA = c->planes + kPlaneTLO * pe;
+      a.RB = c->planes + kPlaneTUP * pe;
+      a.prev = K == 1 ? in : c->xb;
+      a.rsum = rsum;
+    }
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
     CK(launch_sweeps_fused(a, coupled, c->nb_fused, s));
     if (ev && final) CK(cudaEventRecord(ev[1], s));
-    CK(launch_fused_scale(c->flsum, L, K, scale, scale + 2, &c->hdr->ticket[4], s));
+    CK(launch_fused_scale(c->flsum, L, K, with_resid ? rsum : nullptr, a.P0, scale, scale + 4,
+                          &c->hdr->ticket[4], s));
     if (ev && final) CK(cudaEventRecord(ev[2], s));
     NormArgs nn{};
+    nn.r = with_resid ? scale + 2 : nullptr;
     // step error of the last sweep: z_K / s_K against z_{K-1} / s_{K-1}
     // (block-tridiagonal: z_K in Z, z_{K-1} in W; block-banded: z_k in W for
     // odd k, in Z for even k >= 2)
@@ -232,10 +251,12 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
 
 // nsweeps sweeps src -> dst (in place allowed).  Stair splittings run as
 // fused launches; the comparison splittings one sweep at a time, each
-// normalised.
+// normalised.  resid: form ||Q^T dst||_1 from the splitting (stats[2]) where
+// split_resid_ok.
 static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
-                          double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr) {
-  if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev);
+                          double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr,
+                          bool resid = false) {
+  if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev, resid);
   for (int64_t k = 0; k < n; ++k) {
     const int rc = enqueue_sweep(c, k == 0 ? src : dst, dst, k == n - 1 ? stats_out : nullptr, s,
                                  ev ? ev + 4 * k : nullptr);
@@ -244,7 +265,8 @@ static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n
   return MC_OK;
 }
 
-static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float* q = nullptr) {
+static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float* q = nullptr,
+                            double* out = nullptr) {
   const size_t pe = c->lay.plane_bytes / sizeof(double);
   ResidArgs r{};
   r.TLO = c->planes + kPlaneTLO * pe;
@@ -255,7 +277,7 @@ static int enqueue_residual(mc_chain* c, const double* x, cudaStream_t s, float*
   r.x = x;
   r.rpart = c->rpart;
   r.hdr = c->hdr;
-  r.out = nullptr;
+  r.out = out;
   r.L = c->lay.L;
   r.m = c->lay.m;
   r.ms = c->lay.ms;
@@ -508,7 +530,11 @@ int mc_sweep(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, do
   if (!c || !x_in || !x_out || nsweeps < 1) return MC_ERR_ARG;
   if (((uintptr_t)x_in | (uintptr_t)x_out) & 7u) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
-  return enqueue_sweeps(c, x_in, x_out, nsweeps, stats_dev, c->user);
+  const bool split = split_resid_ok(c);
+  const int rc = enqueue_sweeps(c, x_in, x_out, nsweeps, stats_dev, c->user, nullptr,
+                                stats_dev != nullptr && split);
+  if (rc != MC_OK || !stats_dev || split) return rc;
+  return enqueue_residual(c, x_out, c->user, nullptr, stats_dev + 2);
 }
 
 int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, double* ms_host) {
@@ -539,7 +565,7 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
     for (int q = 1; q < 4 && rc == MC_OK; ++q)
       if (cudaEventRecord(ev[q], c->user) != cudaSuccess) rc = MC_ERR_CUDA;
   } else {
-    rc = enqueue_sweeps(c, x_in, x_out, nsweeps, nullptr, c->user, ev);
+    rc = enqueue_sweeps(c, x_in, x_out, nsweeps, nullptr, c->user, ev, split_resid_ok(c));
   }
   double t[3] = {0.0, 0.0, 0.0};
   if (rc == MC_OK && cudaStreamSynchronize(c->user) != cudaSuccess) rc = MC_ERR_CUDA;
@@ -571,24 +597,37 @@ int mc_profile(mc_chain* c, const double* x_in, double* x_out, int64_t nsweeps, 
   return sync_header(c);
 }
 
+// Device address of a page-locked host buffer (16-byte aligned), or NULL for
+// pageable memory.  Kernels read and write such buffers directly over the
+// CPU-GPU link (NVLink-C2C on Grace-Blackwell), so no staging copy is needed.
+static const double* mapped(const double* h) {
+  cudaPointerAttributes pa{};
+  if (cudaPointerGetAttributes(&pa, h) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (pa.type == cudaMemoryTypeHost && pa.devicePointer && ((uintptr_t)pa.devicePointer & 15u) == 0)
+    return (const double*)pa.devicePointer;
+  return nullptr;
+}
+
 int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int64_t nsweeps,
                   double* stats_host) {
   if (!c || !x_in_host || !x_out_host || nsweeps < 1) return MC_ERR_ARG;
   if (!c->factored) return MC_ERR_NOT_FACTORED;
   const size_t bytes = (size_t)c->lay.N * sizeof(double);
-  // page-locked output buffer: the final normalisation stores the result
-  // straight into it (one fused launch; no separate device-to-host copy)
-  double* out_dev = nullptr;
-  cudaPointerAttributes pa{};
-  if (cudaPointerGetAttributes(&pa, x_out_host) == cudaSuccess) {
-    if (pa.type == cudaMemoryTypeHost && pa.devicePointer &&
-        ((uintptr_t)pa.devicePointer & 15u) == 0 && fused_ok(c) && nsweeps <= kMaxFusedSweeps)
-      out_dev = (double*)pa.devicePointer;
-  } else {
-    cudaGetLastError();
-  }
-  CK(cudaMemcpyAsync(c->xa, x_in_host, bytes, cudaMemcpyHostToDevice, c->user));
-  const int rc = enqueue_sweeps(c, c->xa, out_dev ? out_dev : c->xa, nsweeps, nullptr, c->user);
+  // page-locked input: the first half-sweep (and the step error) read it in
+  // place; page-locked output: the final normalisation stores the result
+  // straight into it (one fused launch).  Pageable buffers are copied.
+  const double* in_dev = fused_ok(c) ? mapped(x_in_host) : nullptr;
+  double* out_dev = (fused_ok(c) && nsweeps <= kMaxFusedSweeps) ? (double*)mapped(x_out_host)
+                                                                 : nullptr;
+  if (!in_dev) CK(cudaMemcpyAsync(c->xa, x_in_host, bytes, cudaMemcpyHostToDevice, c->user));
+  const bool split = split_resid_ok(c);
+  double* res_dev = out_dev ? out_dev : c->xa;
+  int rc = enqueue_sweeps(c, in_dev ? in_dev : c->xa, res_dev, nsweeps, nullptr, c->user, nullptr,
+                          stats_host != nullptr && split);
+  if (rc == MC_OK && stats_host && !split) rc = enqueue_residual(c, res_dev, c->user);
   if (rc != MC_OK) return rc;
   if (!out_dev)
     CK(cudaMemcpyAsync(x_out_host, c->xa, bytes, cudaMemcpyDeviceToHost, c->user));
@@ -596,20 +635,29 @@ int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int6
   if (stats_host) {
     stats_host[0] = c->hh->stats[0];
     stats_host[1] = c->hh->stats[1];
-    stats_host[2] = nan("");
+    stats_host[2] = c->hh->stats[2];
   }
   return st;
 }
 
-static int capture_chunk(mc_chain* c, int chunk, int with_resid) {
+// Residual of a chunk of mc_solve: none, direct (k_residual after the sweeps)
+// or from the splitting inside the last fused launch.
+enum { kResidNone = 0, kResidDirect = 1, kResidSplit = 3 };
+
+// The sweeps (and residual) of one chunk of mc_solve on xa, in place.
+static int enqueue_chunk(mc_chain* c, int64_t chunk, int resid_mode, cudaStream_t s) {
+  int rc = enqueue_sweeps(c, c->xa, c->xa, chunk, nullptr, s, nullptr, resid_mode == kResidSplit);
+  if (rc == MC_OK && resid_mode == kResidDirect) rc = enqueue_residual(c, c->xa, s);
+  return rc;
+}
+
+static int capture_chunk(mc_chain* c, int chunk, int resid_mode) {
   if (c->gexec) {
     cudaGraphExecDestroy(c->gexec);
     c->gexec = nullptr;
   }
   CK(cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal));
-  int rc = MC_OK;
-  rc = enqueue_sweeps(c, c->xa, c->xa, chunk, nullptr, c->cap);
-  if (rc == MC_OK && with_resid) rc = enqueue_residual(c, c->xa, c->cap);
+  int rc = enqueue_chunk(c, chunk, resid_mode, c->cap);
   if (rc == MC_OK &&
       cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->cap) != cudaSuccess)
     rc = MC_ERR_CUDA;
@@ -627,7 +675,7 @@ static int capture_chunk(mc_chain* c, int chunk, int with_resid) {
     return MC_ERR_CUDA;
   }
   c->g_chunk = chunk;
-  c->g_resid = with_resid;
+  c->g_resid = resid_mode;
   return MC_OK;
 }
 
@@ -720,28 +768,27 @@ int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, 
   int st = sync_header(c);
   if (st != MC_OK) return st;
   if (c->lay.lp) return solve_refine(c, pi, tol, eps, maxit, check_every, res);
-  const int with_resid = tol > 0.0;
+  // residual test every chunk: from the splitting inside the chunk's last
+  // fused launch (block-tridiagonal stair splittings; confirmed once by the
+  // direct residual before stopping) or the direct residual
+  const int mode = tol > 0.0 ? (split_resid_ok(c) ? kResidSplit : kResidDirect) : kResidNone;
   int64_t k = 0;
   double d = NAN, d_prev = NAN, r = NAN, kappa = NAN;
   int converged = 0;
+  bool direct = mode == kResidDirect;   // r is the direct residual of xa
   while (k < maxit) {
     const int64_t chunk = (maxit - k < check_every) ? (maxit - k) : check_every;
+    direct = mode == kResidDirect;
     if (chunk == check_every) {
-      if (!c->gexec || c->g_chunk != check_every || c->g_resid != with_resid) {
-        const int rc = capture_chunk(c, check_every, with_resid);
+      if (!c->gexec || c->g_chunk != check_every || c->g_resid != mode) {
+        const int rc = capture_chunk(c, check_every, mode);
         if (rc != MC_OK) return rc;
       }
       CK(cudaGraphLaunch(c->gexec, c->user));
       CK(cudaStreamSynchronize(c->user));
     } else {
-      {
-        const int rc = enqueue_sweeps(c, c->xa, c->xa, chunk, nullptr, c->user);
-        if (rc != MC_OK) return rc;
-      }
-      if (with_resid) {
-        const int rc = enqueue_residual(c, c->xa, c->user);
-        if (rc != MC_OK) return rc;
-      }
+      const int rc = enqueue_chunk(c, chunk, mode, c->user);
+      if (rc != MC_OK) return rc;
       CK(cudaMemcpyAsync(c->hh, c->hdr, sizeof(Header), cudaMemcpyDeviceToHost, c->user));
       CK(cudaStreamSynchronize(c->user));
     }
@@ -753,16 +800,27 @@ int mc_solve(mc_chain* c, const double* x0, double* pi, double tol, double eps, 
       return st;
     }
     d = c->hh->stats[1];
-    if (with_resid) r = c->hh->stats[2];
+    if (mode != kResidNone) r = c->hh->stats[2];
     if (d_prev > 0.0 && d > 0.0) kappa = pow(d / d_prev, 1.0 / (double)chunk);
     d_prev = d;
-    if ((with_resid && r <= tol) || (eps > 0.0 && d <= eps)) {
+    if (mode == kResidSplit && r <= tol) {
+      // confirm with the direct residual of the stored iterate (the two agree
+      // to rounding; near the rounding floor the direct one decides)
+      const int rc = enqueue_residual(c, c->xa, c->user);
+      if (rc != MC_OK) return rc;
+      st = sync_header(c);
+      if (st != MC_OK) return st;
+      r = c->hh->stats[2];
+      direct = true;
+    }
+    if ((mode != kResidNone && r <= tol) || (eps > 0.0 && d <= eps)) {
       converged = 1;
       break;
     }
   }
   CK(cudaMemcpyAsync(pi, c->xa, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice, c->user));
-  if (!with_resid) {
+  if (!direct) {
+    // the reported residual is always the direct one of the returned pi
     const int rc = enqueue_residual(c, c->xa, c->user);
     if (rc != MC_OK) return rc;
     st = sync_header(c);

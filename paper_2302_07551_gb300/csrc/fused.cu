@@ -21,6 +21,15 @@
 // expiry the warp latches MC_ERR_TIMEOUT and carries on, so the launch
 // always ends.
 //
+// Residual of the result (with_resid): P0 more units follow the K sweeps in
+// the queue, one per diagonal-only level l.  The last sweep solved
+// M z_K = N z_{K-1}, so Q^T z_K = N (z_{K-1} - z_K): zero on the coupled rows
+// and T_lo d_{l-1} + T_up d_{l+1} (d = z_K - z_{K-1}) on the diagonal-only
+// rows.  A residual unit waits until both neighbours hold z_K, reads z_K from
+// Z and z_{K-1} from W (x_in when K = 1) and stores its level's L1 norm; this
+// streams the off-diagonal blocks of half the levels once, a third of one
+// sweep's bytes in inverse mode, instead of all three blocks of every level.
+//
 // Values and level sums do not depend on which warp handles which unit, and
 // the sums are reduced per level in a fixed order: results are bitwise
 // reproducible for any grid.
@@ -41,12 +50,24 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
   extern __shared__ double vsh[];
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
-  const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
+  const unsigned long long sweeps = (unsigned long long)a.K * (unsigned long long)a.L;
+  const unsigned long long total = sweeps + (a.with_resid ? (unsigned long long)a.P0 : 0ull);
   unsigned long long q0 = claim_unit(a.claim, lane);
   unsigned long long q = __shfl_sync(kFull, q0, 0);
   while (q < total) {
     // claim the next unit now; its index is needed only after this one
     q0 = claim_unit(a.claim, lane);
+    if (q >= sweeps) {
+      // residual unit of diagonal-only level l: neighbours must hold z_K
+      const int64_t u = (int64_t)(q - sweeps);
+      const int64_t l = 2 * u + a.par0;
+      wait_neighbours(a.ver, l, a.L, (int)a.K, &a.hdr->status, lane, a.wait_ns);
+      const double t = level_resid_split<R, PAIRED>(a.RA, a.RB, a.Z, a.prev, l, a.L, a.m, a.ms,
+                                                    slice, lane);
+      if (lane == 0) a.rsum[u] = t;
+      q = __shfl_sync(kFull, q0, 0);
+      continue;
+    }
     const int64_t k = (int64_t)(q / (unsigned long long)a.L);
     const int64_t r = (int64_t)q - k * a.L;
     const bool h2 = r >= a.P0;
@@ -111,12 +132,14 @@ __global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* 
   wait_neighbours(ver, 1, 3, 1, &hdr->status, lane, wait_ns);
 }
 
-// e^T z_K and e^T z_{K-1} from the per-level sums.  FP64 adds run at two
-// lanes per clock per SM here, so the sums are spread over kScaleBlocks
-// blocks, each over a fixed contiguous range of levels; the last block to
-// finish adds the block partials (fixed summation order).
-// part: 2 kScaleBlocks doubles of scratch; ticket: zero between launches.
+// e^T z_K and e^T z_{K-1} from the per-level sums, and the residual from the
+// per-level residual norms.  FP64 adds run at two lanes per clock per SM
+// here, so the sums are spread over kScaleBlocks blocks, each over a fixed
+// contiguous range of levels; the last block to finish adds the block
+// partials (fixed summation order).
+// part: 3 kScaleBlocks doubles of scratch; ticket: zero between launches.
 __global__ void __launch_bounds__(256) k_fused_scale(const double* lsum, int64_t L, int64_t K,
+                                                     const double* rsum, int64_t P,
                                                      double* part, unsigned* ticket,
                                                      double* out) {
   __shared__ double sh[32];
@@ -126,16 +149,24 @@ __global__ void __launch_bounds__(256) k_fused_scale(const double* lsum, int64_t
   const int64_t chunk = (L + gridDim.x - 1) / gridDim.x;
   const int64_t l0 = blockIdx.x * chunk;
   const int64_t l1 = l0 + chunk < L ? l0 + chunk : L;
-  double ta = 0.0, tb = 0.0;
+  double ta = 0.0, tb = 0.0, tr = 0.0;
   for (int64_t l = l0 + threadIdx.x; l < l1; l += blockDim.x) {
     ta += a[l];
     if (K >= 2) tb += b[l];
   }
+  if (rsum) {
+    const int64_t pc = (P + gridDim.x - 1) / gridDim.x;
+    const int64_t p0 = blockIdx.x * pc;
+    const int64_t p1 = p0 + pc < P ? p0 + pc : P;
+    for (int64_t u = p0 + threadIdx.x; u < p1; u += blockDim.x) tr += rsum[u];
+  }
   ta = block_sum(ta, sh);
   tb = block_sum(tb, sh);
+  tr = block_sum(tr, sh);
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = ta;
-    part[2 * blockIdx.x + 1] = tb;
+    part[3 * blockIdx.x] = ta;
+    part[3 * blockIdx.x + 1] = tb;
+    part[3 * blockIdx.x + 2] = tr;
     __threadfence();
     last = atomicAdd(ticket, 1u) == gridDim.x - 1;
   }
@@ -144,16 +175,19 @@ __global__ void __launch_bounds__(256) k_fused_scale(const double* lsum, int64_t
   __threadfence();
   // the first warp loads the partials in parallel (lane i: blocks i, i + 32)
   // and adds them with a fixed shuffle tree
-  double sa = 0.0, sb = 0.0;
+  double sa = 0.0, sb = 0.0, sr = 0.0;
   for (int i = threadIdx.x; i < (int)gridDim.x; i += 32) {
-    sa += __ldcg(part + 2 * i);
-    sb += __ldcg(part + 2 * i + 1);
+    sa += __ldcg(part + 3 * i);
+    sb += __ldcg(part + 3 * i + 1);
+    sr += __ldcg(part + 3 * i + 2);
   }
   sa = warp_sum(sa);
   sb = warp_sum(sb);
+  sr = warp_sum(sr);
   if (threadIdx.x == 0) {
     out[0] = sa;
     out[1] = K >= 2 ? sb : 1.0;
+    out[2] = rsum ? sr : nan("");
     *ticket = 0u;
   }
 }
@@ -238,9 +272,10 @@ cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header*
   return cudaGetLastError();
 }
 
-cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
-                               double* part, unsigned* ticket, cudaStream_t s) {
-  k_fused_scale<<<kScaleBlocks, 256, 0, s>>>(lsum, L, K, part, ticket, out);
+cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, const double* rsum,
+                               int64_t P, double* out, double* part, unsigned* ticket,
+                               cudaStream_t s) {
+  k_fused_scale<<<kScaleBlocks, 256, 0, s>>>(lsum, L, K, rsum, P, part, ticket, out);
   return cudaGetLastError();
 }
 

@@ -58,8 +58,9 @@ struct Layout {
   int far_base;          // plane index of the first far diagonal
   size_t plane_bytes, vec_bytes;
   size_t off_hdr, off_planes, off_z, off_xa, off_xb, off_wpart, off_dpart, off_rpart, total;
-  // fused multi-sweep launches: per-level sums of the last two sweeps (+ the
-  // two scales), queue counter + per-level completion counters
+  // fused multi-sweep launches: per-level sums of the last two sweeps, the
+  // per-level residual sums, the scales, queue counter + per-level completion
+  // counters
   size_t off_fsum, off_fver;
   // low-precision storage (dtype MC_F32 / MC_BF16)
   int lp;                // 0: none, 1: FP32, 2: BF16
@@ -119,9 +120,21 @@ struct FusedArgs {
   // Z (sweep k writes W for even k, Z for odd k) instead of updating in place
   const FarDesc* far;
   int bw;
+  // residual of z_K from the splitting (block-tridiagonal stair splittings):
+  // with_resid adds P0 units after the K sweeps, one per diagonal-only level
+  // l, each storing ||T_lo (z_K - z_{K-1})_{l-1} + T_up (z_K - z_{K-1})_{l+1}||_1
+  // into rsum[(l - par0) / 2] (Q^T z_K = N (z_{K-1} - z_K) is zero on the
+  // coupled rows).  RA, RB: the T_lo, T_up planes; prev: z_{K-1} (W, or x_in
+  // when K = 1).
+  int with_resid;
+  const double* RA;
+  const double* RB;
+  const double* prev;
+  double* rsum;
 };
 
 struct NormArgs {
+  const double* r;       // NULL, or ||Q^T z||_1 (stats[2] = *r / e^T z)
   const double* z;
   const double* x_old;   // NULL: no step error (the previous iterate was not stored)
   const double* s_old;   // NULL: x_old is normalised; else x_old / *s_old is the iterate
@@ -169,11 +182,13 @@ cudaError_t launch_sweeps_fused(const FusedArgs& a, int coupled, int n_blocks, c
 // MC_ERR_TIMEOUT is latched in hdr when they never do.
 cudaError_t launch_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver,
                                  cudaStream_t s);
-// out[0] = e^T z_K, out[1] = e^T z_{K-1} (1 when K = 1), fixed summation order;
-// part: 2 kScaleBlocks doubles of scratch, ticket: a counter that is zero.
+// out[0] = e^T z_K, out[1] = e^T z_{K-1} (1 when K = 1), out[2] = the sum of
+// rsum[0..P) (NaN when rsum is NULL), fixed summation order; part:
+// 3 kScaleBlocks doubles of scratch, ticket: a counter that is zero.
 constexpr int kScaleBlocks = 64;
-cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, double* out,
-                               double* part, unsigned* ticket, cudaStream_t s);
+cudaError_t launch_fused_scale(const double* lsum, int64_t L, int64_t K, const double* rsum,
+                               int64_t P, double* out, double* part, unsigned* ticket,
+                               cudaStream_t s);
 cudaError_t launch_residual(const ResidArgs& a, int n_blocks, cudaStream_t s);
 cudaError_t launch_fill(double* x, int64_t n, double v, cudaStream_t s);
 // Latch MC_ERR_ARG unless the paired zero quadrants of TLO / TUP are zero.

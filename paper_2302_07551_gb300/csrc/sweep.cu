@@ -174,13 +174,15 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
     if (threadIdx.x == 0) {
       // e^T z relative to the previous iterate (s itself when that was normalised)
       const double sr = s / so;
+      // ||Q^T z||_1 / e^T z = ||Q^T x_new||_1
+      const double res = a.r ? *a.r * inv : nan("");
       a.hdr->stats[0] = sr;
       a.hdr->stats[1] = e;
-      a.hdr->stats[2] = nan("");
+      a.hdr->stats[2] = res;
       if (a.stats_out) {
         a.stats_out[0] = sr;
         a.stats_out[1] = e;
-        a.stats_out[2] = nan("");
+        a.stats_out[2] = res;
       }
       a.hdr->ticket[0] = 0u;
     }

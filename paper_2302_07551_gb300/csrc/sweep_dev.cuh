@@ -247,6 +247,49 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
   return total;
 }
 
+// Residual of a sweep's result at a diagonal-only stair row l, from the
+// splitting instead of a product with all three blocks: the sweep solved
+// M z = N x, so Q^T z = M z - N z = N (x - z), which is zero on the coupled
+// rows (N has no entries there) and equals T_lo d_{l-1} + T_up d_{l+1},
+// d = z - x, on the diagonal-only rows.  z, x: the sweep's result and input
+// (written by other SMs during the launch: read from L2).  d is small near
+// convergence, so its product rounds far below the direct residual's
+// cancellation.  Returns ||(Q^T z)_l||_1 on every lane.
+template <int R, bool PAIRED>
+__device__ __forceinline__ double level_resid_split(const double* TLO, const double* TUP,
+                                                    const double* z, const double* x, int64_t l,
+                                                    int64_t L, int m, int ms, double* slice,
+                                                    int lane) {
+  constexpr int NA = Tune<R>::NA, W = 32 * R;
+  double* v_lo = slice;
+  double* v_up = slice + W;
+  const bool has_lo = l > 0, has_up = l < L - 1;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const int row = lane + 32 * r;
+    if (has_lo)
+      v_lo[row] = row < m ? __ldcg(z + (l - 1) * m + row) - __ldcg(x + (l - 1) * m + row) : 0.0;
+    if (has_up)
+      v_up[row] = row < m ? __ldcg(z + (l + 1) * m + row) - __ldcg(x + (l + 1) * m + row) : 0.0;
+  }
+  __syncwarp();
+  double acc[R][NA];
+  zero_acc<R>(acc);
+  if constexpr (PAIRED) {
+    if (has_lo) gemv_lo_paired<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+    if (has_up) gemv_up_paired<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+  } else {
+    if (has_lo) gemv_acc<R>(acc, TLO + (size_t)l * ms, v_lo, m, lane);
+    if (has_up) gemv_acc<R>(acc, TUP + (size_t)l * ms, v_up, m, lane);
+  }
+  double ls = 0.0;
+#pragma unroll
+  for (int r = 0; r < R; ++r) ls += fabs(fold<R>(acc[r]));
+  const double total = warp_sum(ls);
+  __syncwarp();   // the slice is rewritten for the next level
+  return total;
+}
+
 // One level of the direct residual r_l = (Q^T x)_l = T_lo x_{l-1} + T_dd x_l +
 // T_up x_{l+1} (Eq. (1)); returns ||r_l||_1 on every lane.  With q != NULL
 // also stores q_l = (-T_dd)^{-1} r_l in FP32.

@@ -34,6 +34,8 @@ WORKLOADS = {
     "qbd_L512_m64": dict(kind="qbd", L=512, m=64, ratio=0.9, level_dependent=True, seed=1),
     # same recipe at L=8192 (0.8 GB of blocks per sweep): profiling-size case
     "qbd_L8192_m64": dict(kind="qbd", L=8192, m=64, ratio=0.9, level_dependent=True, seed=1),
+    # same recipe at L=2048 (L/16 of the bench chain): solution parity with the oracle
+    "qbd_L2048_m64": dict(kind="qbd", L=2048, m=64, ratio=0.9, level_dependent=True, seed=1),
     # block Hessenberg: batch arrivals of up to 4 levels, single-level service;
     # L=4096, m=64, level-dependent, up/down rate ratio 0.8, jump rates halve per level
     "hessenberg_L4096_m64": dict(kind="banded", L=4096, m=64, p=1, q=4, ratio=0.8, decay=0.5,
@@ -42,7 +44,9 @@ WORKLOADS = {
     "penta_L8192_m128": dict(kind="penta", L=8192, m=128, ratio=0.8, scale2=0.3, seed=2),
     # same recipe at L=2048 (1024 paired levels of 256; 1.3 GB per sweep): profiling size
     "penta_L2048_m128": dict(kind="penta", L=2048, m=128, ratio=0.8, scale2=0.3, seed=2),
-    # same recipe at L=1024 (time-to-solution comparisons)
+    # same recipe at L=512 (256 paired levels; L/16): solution parity with the oracle
+    "penta_L512_m128": dict(kind="penta", L=512, m=128, ratio=0.8, scale2=0.3, seed=2),
+    # same recipe at L=1024 (L/16 of the m=256 chain): solution parity, time to solution
     "qbd_L1024_m256": dict(kind="qbd", L=1024, m=256, ratio=0.9, level_dependent=True, seed=3),
     # L=16384, m=256, level-dependent, ratio 0.9 (FP64 blocks ~25.8 GB)
     "qbd_L16384_m256": dict(kind="qbd", L=16384, m=256, ratio=0.9, level_dependent=True, seed=3),

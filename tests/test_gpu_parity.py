@@ -84,6 +84,119 @@ def test_iterates_after_fixed_sweeps(L, m, stair, apply):
     ch.close()
 
 
+U = 2.0 ** -53
+
+
+def abs_bound(oc, x):
+    """|| |Q^T| |x| ||_1: the scale of the rounding error of any FP64
+    evaluation of Q^T x (every term of every row summed in absolute value)."""
+    L, m = oc.L, oc.m
+    P = np.abs(np.asarray(x, np.float64)).reshape(L, m)
+    B = 0.0
+    for l in range(L):
+        acc = np.abs(oc.Tdd[l]) @ P[l]
+        if l > 0:
+            acc += np.abs(oc.Tlo[l]) @ P[l - 1]
+        if l < L - 1:
+            acc += np.abs(oc.Tup[l]) @ P[l + 1]
+        B += acc.sum()
+    return B
+
+
+def resid_tol(oc, x, r):
+    """Allowed |r_gpu - r_oracle| for ||Q^T x||_1: both sides are exact up to
+    rounding of sums of at most 3m products (plus, on the GPU, the rounding of
+    the sweep that produced x), each bounded by a small multiple of m u B."""
+    return 1e-12 * r + 8 * oc.m * U * abs_bound(oc, x)
+
+
+@pytest.mark.parametrize("apply", ["inverse", "coupled"])
+@pytest.mark.parametrize("stair", [1, 2])
+@pytest.mark.parametrize("L,m", [(64, 8), (37, 5), (2, 1), (3, 33), (130, 64), (21, 100),
+                                 (9, 256), (11, 160)])
+def test_sweep_residual_from_the_splitting(L, m, stair, apply):
+    """stats[2] of a sweep call is ||Q^T pi||_1 of the returned pi, formed from
+    the splitting (Q^T z = N (x - z), zero on the coupled rows) at the end of
+    the fused launch; it matches the oracle's direct residual of the same pi
+    within the rounding bound (sharp while the residual is far above it)."""
+    blocks, oc = make(L, m, seed=L * 17 + m)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=stair, apply=apply)
+    N = L * m
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    for K in (1, 2, 7, 50):
+        st = torch.zeros(3, dtype=torch.float64, device="cuda")
+        x = ch.sweep(x0, nsweeps=K, stats=st).cpu().numpy()
+        r_gpu = float(st[2])
+        r_or = oc.residual(x)
+        tol = resid_tol(oc, x, r_or)
+        assert abs(r_gpu - r_or) <= tol, (K, r_gpu, r_or, tol)
+        if r_or > 1e3 * tol:       # far from the rounding floor: a sharp check
+            assert abs(r_gpu - r_or) <= 1e-6 * r_or
+    ch.sync()
+    ch.close()
+
+
+@pytest.mark.parametrize("Lp,mp", [(12, 32), (8, 128)])
+def test_paired_sweep_residual_from_the_splitting(Lp, mp):
+    """Paired pentadiagonal chains: the residual products skip the zero
+    quadrants of T_lo / T_up, as the sweep does."""
+    blocks = synth.penta_paired(Lp, mp, 0.8, 0.3, seed=Lp * mp)
+    oc = oracle.Chain(*blocks)
+    ch = mc.Chain(*(dev(b) for b in blocks), paired=True)
+    N = Lp * mp
+    x0 = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    for K in (1, 9):
+        st = torch.zeros(3, dtype=torch.float64, device="cuda")
+        x = ch.sweep(x0, nsweeps=K, stats=st).cpu().numpy()
+        r_or = oc.residual(x)
+        assert abs(float(st[2]) - r_or) <= resid_tol(oc, x, r_or)
+        assert abs(float(st[2]) - r_or) <= 1e-6 * r_or
+    ch.sync()
+    ch.close()
+
+
+def test_solve_stops_at_the_oracles_sweep_with_per_sweep_checks():
+    """check_every = 1: the solve tests the residual (from the splitting,
+    confirmed by the direct residual) after every sweep and stops at the
+    oracle's first sweep with ||Q^T pi||_1 <= tol (unless that residual lies
+    within rounding of tol, where either neighbouring sweep is correct)."""
+    blocks = synth.workload("qbd_L64_m8")
+    oc = oracle.Chain(*blocks)
+    tol = 1e-12
+    ref = oc.solve(tol=tol, maxit=100000, check_every=1)
+    k = ref["sweeps"]
+    N = oc.N
+    r_k = ref["resid"]
+    x_prev = oc.sweeps(np.full(N, 1.0 / N), k - 1)
+    r_prev = oc.residual(x_prev)
+    ch = mc.Chain(*(dev(b) for b in blocks))
+    pi, res = ch.solve(tol=tol, maxit=100000, check_every=1)
+    ch.close()
+    band = resid_tol(oc, ref["x"], tol)
+    if abs(r_k - tol) > band and abs(r_prev - tol) > band:
+        assert res["sweeps"] == k
+    else:
+        assert abs(res["sweeps"] - k) <= 1
+    assert res["converged"] and res["residual"] <= tol
+    assert rel_l1(pi.cpu().numpy(), ref["x"]) <= 1e-10
+
+
+def test_banded_sweep_stats_carry_the_direct_residual():
+    """Block-banded chains (off-staircase terms on every row) report the
+    direct residual of the result in stats[2]."""
+    D = synth.banded(20, 16, 1, 3, 0.8, seed=3)
+    bc = oracle.BandedChain(D)
+    ch = mc.Chain.banded({e: dev(B) for e, B in D.items()})
+    N = 20 * 16
+    st = torch.zeros(3, dtype=torch.float64, device="cuda")
+    x = ch.sweep(torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda"), nsweeps=5,
+                 stats=st).cpu().numpy()
+    r = bc.residual(x)
+    assert abs(float(st[2]) - r) <= 1e-12 * r
+    ch.sync()
+    ch.close()
+
+
 def test_one_sweep_from_random_vector():
     L, m = 33, 48
     blocks, oc = make(L, m, seed=3)
@@ -424,6 +537,8 @@ def test_sweeps_beyond_one_fused_launch():
     assert rel_l1(x.cpu().numpy(), ref) <= 1e-12
     st = stats.cpu().numpy()
     assert abs(st[0] - s) <= 1e-12 * abs(s) and abs(st[1] - d) <= 1e-12
+    r = oc.residual(x.cpu().numpy())
+    assert abs(st[2] - r) <= resid_tol(oc, x.cpu().numpy(), r)
     ch.sync()
     ch.close()
 
@@ -469,6 +584,11 @@ def test_host_buffer_sweeps_equal_device_sweeps(pinned):
         yh = yh.pin_memory() if pinned else yh
         sh = ch.sweep_host(xh, yh, n)
         assert torch.equal(yh, ref) and sh[0] == float(st[0]) and sh[1] == float(st[1])
+        assert sh[2] == float(st[2])
+        zh = torch.empty(N, dtype=torch.float64)
+        zh = zh.pin_memory() if pinned else zh
+        assert ch.sweep_host(xh, zh, n, stats=False) is None     # no residual formed
+        assert torch.equal(zh, ref)
         sh = ch.sweep_host(xh, xh, n)                     # in place
         assert torch.equal(xh, ref)
     ch.sync()
