@@ -580,10 +580,14 @@ def run_serve(args):
 
 
 def run_contraction(args):
-    """Observed contraction factor (step_k / step_{k-w})^(1/w) of the stair
-    splittings, block Jacobi and block Gauss-Seidel on one workload, from the
-    uniform start, with the GPU sweeps/s of each (Sect. 2: on block-tridiagonal
-    Q^T the staircase and block Gauss-Seidel share their spectrum)."""
+    """Observed contraction factor (step_k / step_{k-w})^(1/w), w = the check
+    window, of the stair splittings of type 1 and 2, block Gauss-Seidel (one
+    wavefront-ordered fused launch per window) and block Jacobi on one
+    workload from the uniform start, recorded every --segment sweeps up to
+    --steps (block Jacobi: --bj-steps) so that the approach to the asymptotic
+    rate is visible, with the GPU sweeps/s of each (Sect. 2: on
+    block-tridiagonal Q^T the staircase and block Gauss-Seidel share their
+    spectrum; block Jacobi has the eigenvalue -1 and does not converge)."""
     import torch
 
     import synth
@@ -596,21 +600,33 @@ def run_contraction(args):
     d = [torch.from_numpy(b).cuda() for b in blocks]
     del blocks
     torch.cuda.synchronize()
+    N = L * m
     rows = {}
+    w = min(args.refine_every, 1024)
     for stair, label, nsw in ((1, "stair1", args.steps), (2, "stair2", args.steps),
-                              (3, "block_jacobi", args.steps), (4, "block_gauss_seidel",
-                                                                args.bgs_steps)):
+                              (4, "block_gauss_seidel", args.steps),
+                              (3, "block_jacobi", args.bj_steps)):
         ch = mcl.Chain(*d, stair=stair)
+        x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+        pi = torch.empty_like(x)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, res = ch.solve(tol=0.0, eps=0.0, maxit=nsw, check_every=min(args.refine_every, nsw))
-        torch.cuda.synchronize()
-        t = time.perf_counter() - t0
-        rows[label] = {"sweeps": nsw, "contraction": res["contraction"], "step": res["step"],
-                       "residual": res["residual"], "sweeps_s": nsw / t}
+        traj, done, t = [], 0, 0.0
+        while done < nsw:
+            seg = min(args.segment, nsw - done)
+            t0 = time.perf_counter()
+            _, res = ch.solve(x0=x, tol=0.0, eps=0.0, maxit=seg, check_every=min(w, seg), pi=pi,
+                              raise_on_maxit=False)
+            torch.cuda.synchronize()
+            t += time.perf_counter() - t0
+            done += seg
+            x, pi = pi, x
+            traj.append([done, res["contraction"], res["step"], res["residual"]])
+        rows[label] = {"sweeps": done, "contraction": traj[-1][1], "step": traj[-1][2],
+                       "residual": traj[-1][3], "sweeps_s": done / t,
+                       "trajectory": traj}
         ch.close()
     print(json.dumps({"mode": "contraction", "workload": name, "L": L, "m": m,
-                      "window": args.refine_every, "results": rows}), flush=True)
+                      "window": w, "segment": args.segment, "results": rows}), flush=True)
 
 
 def measure_fp64_peak():
@@ -700,7 +716,9 @@ def main():
     ap.add_argument("--serve", action="store_true", help="serving benchmark on the request stream")
     ap.add_argument("--contraction", action="store_true",
                     help="contraction factors of stair / block Jacobi / block Gauss-Seidel")
-    ap.add_argument("--bgs-steps", type=int, default=200)
+    ap.add_argument("--bj-steps", type=int, default=20000)
+    ap.add_argument("--segment", type=int, default=16384,
+                    help="contraction mode: sweeps between recorded contraction factors")
     ap.add_argument("--requests", type=int, default=16)
     ap.add_argument("--serve-dtype", default="bf16", choices=["f64", "f32", "bf16"])
     ap.add_argument("--serve-tol", type=float, default=1e-10)

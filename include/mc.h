@@ -97,8 +97,12 @@ typedef struct {
   int32_t m;       /* phases per level (block size), 1 <= m <= 256              */
   int32_t stair;   /* 1: stair matrix of type 1 (default), 2: type 2 (Sect. 2);
                       3: block Jacobi, 4: block Gauss-Seidel (the comparison
-                      splittings of Sect. 2; FP64, paired = 0; block Gauss-Seidel
-                      walks the levels in order on one warp, for comparisons)   */
+                      splittings of Sect. 2; FP64, paired = 0).  Block
+                      Gauss-Seidel on block-tridiagonal chains runs all sweeps
+                      of a call in one launch in wavefront order (sweep k at
+                      level l after sweep k at l-1 and sweep k-1 at l+1, up to
+                      min(sweeps, L/2) levels at once); on block-banded chains
+                      one warp walks the levels of one sweep at a time.         */
   int32_t apply;   /* mc_apply                                                  */
   int32_t dtype;   /* mc_dtype (MC_F32 / MC_BF16 need m % 4 == 0)               */
   int32_t paired;  /* 0, or 1: levels are pairs {2J, 2J+1} of a block-pentadiagonal

@@ -156,13 +156,17 @@ constexpr int64_t kMaxFusedSweeps = 1024;
 constexpr unsigned long long kFusedWaitNs = 2000000000ull;
 
 // Stair splittings run fused (block-tridiagonal in place, block-banded with
-// alternating buffers); block Jacobi / Gauss-Seidel one sweep at a time.
-static bool fused_ok(const mc_chain* c) { return c->d.stair <= 2; }
+// alternating buffers), and so does block Gauss-Seidel on block-tridiagonal
+// chains (wavefront order); block Jacobi and banded block Gauss-Seidel one
+// sweep at a time.
+static bool fused_ok(const mc_chain* c) {
+  return c->d.stair <= 2 || (c->d.stair == 4 && c->lay.nfar == 0 && !c->d.paired);
+}
 
 // Block-tridiagonal stair splittings get the residual of a fused launch's
 // result from the splitting (residual units at the end of the launch); other
 // chains use the direct residual.
-static bool split_resid_ok(const mc_chain* c) { return fused_ok(c) && c->lay.nfar == 0; }
+static bool split_resid_ok(const mc_chain* c) { return c->d.stair <= 2 && c->lay.nfar == 0; }
 
 // n stair sweeps src -> dst (in place allowed) as fused launches of at most
 // kMaxFusedSweeps sweeps, each followed by the normalisation (with the step
@@ -211,7 +215,8 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     a.wait_ns = kFusedWaitNs;
     a.far = banded ? (const FarDesc*)((const char*)c->hdr + kFarDescOffset) : nullptr;
     a.bw = bw;
-    const bool with_resid = resid && final && !banded;
+    a.bgs = c->d.stair == 4;
+    const bool with_resid = resid && final && !banded && !a.bgs;
     if (with_resid) {
       a.with_resid = 1;
       a.RA = c->planes + kPlaneTLO * pe;
@@ -219,8 +224,16 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
       a.prev = K == 1 ? in : c->xb;
       a.rsum = rsum;
     }
+    // block Gauss-Seidel runs at most min(K, L/2) units at once (one per sweep
+    // in flight): twice that many warps keep the next diagonal claimed
+    int nb = c->nb_fused;
+    if (a.bgs) {
+      const int64_t par = K < (L + 1) / 2 ? K : (L + 1) / 2;
+      const int64_t nbw = (2 * par + 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      if (nbw < nb) nb = (int)nbw;
+    }
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
-    CK(launch_sweeps_fused(a, coupled, c->nb_fused, s));
+    CK(launch_sweeps_fused(a, coupled, nb, s));
     if (ev && final) CK(cudaEventRecord(ev[1], s));
     CK(launch_fused_scale(c->flsum, L, K, with_resid ? rsum : nullptr, a.P0, scale, scale + 4,
                           &c->hdr->ticket[4], s));

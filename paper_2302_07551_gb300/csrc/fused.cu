@@ -123,6 +123,38 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs 
   }
 }
 
+// Block Gauss-Seidel sweeps (Sect. 2 comparison splitting, M = block lower
+// triangle of Q^T), all K sweeps of a call in one persistent launch:
+// z^{k+1}_l = (-T_dd)^{-1} (T_lo z^{k+1}_{l-1} + T_up z^k_{l+1}) (inverse mode;
+// W_lo, W_up when coupled).  Unit (k, l) needs (k, l-1) and (k-1, l+1), so the
+// units are claimed in wavefront order (wave_unit): a sweep traverses the
+// levels one after the other, each sweep trailing the previous one by two
+// levels, and up to min(K, L / 2) units run at once.  In place in W (the
+// last sweep writes Z): a unit overwrites z^k_l only after its two readers,
+// (k, l-1) and (k-1, l+1), have completed, which is what it waits for.
+template <int R, bool COUPLED>
+__global__ void __launch_bounds__(256, Tune<R>::MINB) k_bgs_fused(FusedArgs a) {
+  extern __shared__ double vsh[];
+  const int lane = threadIdx.x & 31;
+  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
+  const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
+  unsigned long long q0 = claim_unit(a.claim, lane);
+  unsigned long long q = __shfl_sync(kFull, q0, 0);
+  while (q < total) {
+    q0 = claim_unit(a.claim, lane);
+    int64_t k, l;
+    wave_unit(q, a.L, a.K, &k, &l);
+    double* dst = k == a.K - 1 ? a.Z : a.W;
+    const double* up = k == 0 ? a.x_in : a.W;    // z^k at l + 1
+    wait_neighbours2(a.ver, l, a.L, (int)(k + 1), (int)k, &a.hdr->status, lane, a.wait_ns);
+    const double t = level_sweep2<R, COUPLED, false, true, true>(a.A, a.B, a.C, dst, up, dst, l,
+                                                                 a.L, a.m, a.ms, slice, lane);
+    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+    publish(a.ver + l, (int)(k + 1), lane);
+    q = __shfl_sync(kFull, q0, 0);
+  }
+}
+
 // Self-test of the bounded wait: one warp waits for level 1 of a 3-level
 // counter array; the counters hold `preset`, the wait needs 1.
 __global__ void k_wait_selftest(int preset, unsigned long long wait_ns, Header* hdr, int* ver) {
@@ -207,6 +239,21 @@ cudaError_t sweeps_r(const FusedArgs& a, int nb, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+template <int R, bool C>
+cudaError_t bgs_fused_r(const FusedArgs& a, int nb, cudaStream_t s) {
+  static bool done = false;
+  const size_t smem = (size_t)kWarpsPerBlock * 3 * 32 * R * sizeof(double);
+  if (!done && smem > 40 * 1024) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_bgs_fused<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  k_bgs_fused<R, C><<<nb, 256, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 template <int R>
 cudaError_t banded_r(const FusedArgs& a, int nb, cudaStream_t s) {
   static bool done = false;
@@ -224,6 +271,20 @@ cudaError_t banded_r(const FusedArgs& a, int nb, cudaStream_t s) {
 
 template <bool C>
 cudaError_t sweeps_dispatch(const FusedArgs& a, int nb, cudaStream_t s) {
+  if (a.bgs) {
+    if (a.far || a.paired) return cudaErrorInvalidValue;
+    switch ((a.m + 31) / 32) {
+      case 1: return bgs_fused_r<1, C>(a, nb, s);
+      case 2: return bgs_fused_r<2, C>(a, nb, s);
+      case 3: return bgs_fused_r<3, C>(a, nb, s);
+      case 4: return bgs_fused_r<4, C>(a, nb, s);
+      case 5: return bgs_fused_r<5, C>(a, nb, s);
+      case 6: return bgs_fused_r<6, C>(a, nb, s);
+      case 7: return bgs_fused_r<7, C>(a, nb, s);
+      case 8: return bgs_fused_r<8, C>(a, nb, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   if (a.far) {
     if (C) return cudaErrorInvalidValue;   // block-banded chains: inverse mode only
     switch ((a.m + 31) / 32) {

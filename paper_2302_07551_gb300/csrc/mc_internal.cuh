@@ -127,6 +127,9 @@ struct FusedArgs {
   // coupled rows).  RA, RB: the T_lo, T_up planes; prev: z_{K-1} (W, or x_in
   // when K = 1).
   int with_resid;
+  // block Gauss-Seidel instead of a stair splitting (block-tridiagonal, not
+  // paired): units in wavefront order, in place (k_bgs_fused)
+  int bgs;
   const double* RA;
   const double* RB;
   const double* prev;

@@ -60,6 +60,65 @@ __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64
   if (up) (void)ld_acquire(ver + l + 1);
 }
 
+// As wait_neighbours with separate counts for the two neighbours: level l-1
+// must have completed need_lo writes and level l+1 need_up (<= 0: no wait).
+__device__ __forceinline__ void wait_neighbours2(const int* ver, int64_t l, int64_t L,
+                                                 int need_lo, int need_up, int* status, int lane,
+                                                 unsigned long long wait_ns) {
+  const bool lo = l > 0 && need_lo > 0, up = l < L - 1 && need_up > 0;
+  if (lane == 0) {
+    unsigned long long t0 = 0;
+    for (int it = 0;; ++it) {
+      const bool ok = (!lo || ld_acquire(ver + l - 1) >= need_lo) &&
+                      (!up || ld_acquire(ver + l + 1) >= need_up);
+      if (ok) break;
+      if (it == 0) {
+        t0 = global_ns();
+      } else if (global_ns() - t0 > wait_ns) {
+        atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
+        break;
+      }
+      __nanosleep(128);
+    }
+  }
+  __syncwarp();
+  if (lo) (void)ld_acquire(ver + l - 1);
+  if (up) (void)ld_acquire(ver + l + 1);
+}
+
+// Wavefront order of the units (sweep k, level l), 0 <= k < K, 0 <= l < L,
+// of fused block Gauss-Seidel sweeps: by anti-diagonal t = 2k + l, then k.
+// Unit (k, l) needs (k, l-1) and (k-1, l+1), both on diagonal t - 1, so every
+// unit depends only on units earlier in the order, and the units of one
+// diagonal are independent.  wave_prefix(t) counts the units with 2k + l < t:
+// the sweeps k with 2k + L <= t contribute L levels each, those with
+// 2k < t < 2k + L contribute t - 2k.
+__device__ __forceinline__ int64_t wave_prefix(int64_t t, int64_t L, int64_t K) {
+  int64_t a = t >= L ? (t - L) / 2 + 1 : 0;
+  if (a > K) a = K;
+  int64_t b = (t + 1) / 2;
+  if (b > K) b = K;
+  return a * L + (b - a) * t - (b - a) * (a + b - 1);
+}
+
+// Queue position q (< K L) -> (k, l) in wavefront order: the diagonal by
+// bisection on wave_prefix, then the sweep within it.
+__device__ __forceinline__ void wave_unit(unsigned long long q, int64_t L, int64_t K, int64_t* k,
+                                          int64_t* l) {
+  const int64_t qq = (int64_t)q;
+  int64_t lo = 0, hi = 2 * (K - 1) + L;   // wave_prefix(lo) <= q < wave_prefix(hi)
+  while (hi - lo > 1) {
+    const int64_t mid = (lo + hi) / 2;
+    if (wave_prefix(mid, L, K) <= qq)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  const int64_t k0 = lo >= L ? (lo - L + 2) / 2 : 0;   // first sweep on diagonal lo
+  *k = k0 + (qq - wave_prefix(lo, L, K));
+  *l = lo - 2 * *k;
+}
+
 // Block-banded dataflow: wait until every level j in [l - bw, l + bw] has
 // completed `need` writes and, when near_need > need, levels l - 1 and l + 1
 // have completed near_need; lane i polls level l - bw + i (2 bw + 1 <= 32).

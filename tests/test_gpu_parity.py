@@ -478,6 +478,47 @@ def test_block_jacobi_and_gauss_seidel_sweeps(stair, meth, L, m):
     ch.close()
 
 
+@pytest.mark.parametrize("apply", ["inverse", "coupled"])
+@pytest.mark.parametrize("L,m", [(64, 8), (37, 5), (2, 1), (3, 33), (130, 64), (9, 256),
+                                 (11, 160), (300, 16)])
+def test_fused_block_gauss_seidel_sweeps(L, m, apply):
+    """Block Gauss-Seidel sweeps in one wavefront-ordered fused launch: the
+    iterates, e^T z, the step error and the (direct) residual of the last
+    sweep as the oracle's, out of place and in place."""
+    blocks, oc = make(L, m, seed=L * 5 + m)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=4, apply=apply)
+    N = L * m
+    x0 = np.random.default_rng(L + m).random(N)
+    x0 /= x0.sum()
+    for K in (1, 2, 50):
+        prev = oc.sweeps(x0, K - 1, method=oracle.BGS) if K > 1 else x0
+        ref, s, d = oc.normalised_sweep(prev, oracle.BGS)
+        for in_place in (False, True):
+            x = dev(x0.copy())
+            st = torch.zeros(3, dtype=torch.float64, device="cuda")
+            out = ch.sweep(x, x if in_place else None, nsweeps=K, stats=st).cpu().numpy()
+            assert rel_l1(out, ref) <= 1e-12, (K, in_place)
+            g = st.cpu().numpy()
+            assert abs(g[0] - s) <= 1e-12 * abs(s) and abs(g[1] - d) <= 1e-12
+            r = oc.residual(out)
+            assert abs(g[2] - r) <= 1e-12 * r
+    ch.sync()
+    ch.close()
+
+
+def test_fused_block_gauss_seidel_beyond_one_launch():
+    """More block Gauss-Seidel sweeps than one fused launch takes (1024)."""
+    L, m, K = 24, 8, 1100
+    blocks, oc = make(L, m, seed=23)
+    ch = mc.Chain(*(dev(b) for b in blocks), stair=4)
+    N = L * m
+    x = ch.sweep(torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda"), nsweeps=K)
+    ref = oc.sweeps(np.full(N, 1.0 / N), K, method=oracle.BGS)
+    assert rel_l1(x.cpu().numpy(), ref) <= 1e-12
+    ch.sync()
+    ch.close()
+
+
 def test_contraction_stair_equals_gauss_seidel_and_jacobi_stalls():
     """Sect. 2: on block-tridiagonal Q^T the staircase iteration converges at
     the block Gauss-Seidel rate; block Jacobi has |lambda| = 1 twice."""
