@@ -501,7 +501,7 @@ def test_fused_block_gauss_seidel_sweeps(L, m, apply):
             g = st.cpu().numpy()
             assert abs(g[0] - s) <= 1e-12 * abs(s) and abs(g[1] - d) <= 1e-12
             r = oc.residual(out)
-            assert abs(g[2] - r) <= 1e-12 * r
+            assert abs(g[2] - r) <= resid_tol(oc, out, r)
     ch.sync()
     ch.close()
 
