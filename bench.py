@@ -497,6 +497,26 @@ def run_solve(args):
                       "results": rows}), flush=True)
 
 
+def kernel_summary(trials, hbm_peak, hbm_src):
+    """HBM rate of the batched fused sweep launches from the autotuner's timed
+    chunks (CUDA events around the launches, algorithmic bytes of the live
+    requests): over the kept configurations and over all trials."""
+    if not trials:
+        return None
+    kept = [t for t in trials if t["chosen"]]
+
+    def rate(ts):
+        ms = sum(t["sweep_ms"] for t in ts)
+        return sum(t["sweep_bytes"] for t in ts) / (ms * 1e-3) / 1e9 if ms > 0 else None
+
+    best = max(t["sweep_bytes"] / (t["sweep_ms"] * 1e-3) / 1e9 for t in trials if t["sweep_ms"] > 0)
+    kg = rate(kept)
+    return {"kept_gbs": kg, "kept_frac": kg / hbm_peak if kg else None,
+            "all_trials_gbs": rate(trials), "best_trial_gbs": best,
+            "best_trial_frac": best / hbm_peak, "peak_gbs": hbm_peak, "peak_source": hbm_src,
+            "n_trials": len(trials), "n_signatures": len({t["signature"] for t in trials})}
+
+
 def run_serve(args):
     """Continuous-batching serving on the seeded request stream (first K
     requests): closed-loop capacity, then Poisson arrivals at --load x that
@@ -513,18 +533,23 @@ def run_serve(args):
     blocks = [synth.qbd(r["L"], r["m"], r["ratio"], r["seed"], True) for r in reqs]
     gen_s = time.perf_counter() - t0
     budget = int(args.budget_gb * (1 << 30))
+    # batched forms separate the gains of precision (BF16 vs FP64 blocks),
+    # coupling (W = (-T_dd)^{-1} T_lo, ... vs the explicit inverse) and
+    # packing (all requests in shared launches vs one request at a time)
     forms = {
-        "batched_" + args.serve_dtype: dict(dtype=args.serve_dtype, apply=args.apply,
-                                            max_active=1024, autotune=True),
+        "batched_bf16_coupled": dict(dtype="bf16", apply="coupled", max_active=1024, autotune=True),
+        "batched_bf16_inverse": dict(dtype="bf16", apply="inverse", max_active=1024, autotune=True),
+        "batched_f64_coupled": dict(dtype="f64", apply="coupled", max_active=1024, autotune=True),
         "fp64_one_at_a_time": dict(dtype="f64", apply="inverse", max_active=1, autotune=False),
     }
+    hbm_peak, hbm_src = peaks()
     out = {"mode": "serve", "requests": args.requests, "tol": args.serve_tol,
            "budget_gb": args.budget_gb, "load": args.load, "check_every": args.refine_every,
            "stream": "first %d of the seeded stream (L log-uniform [128,16384], m in "
                      "{16,32,64,128}, ratio U(0.5,0.95))" % args.requests,
            "host_generation_s": gen_s, "forms": {}}
     for name, f in forms.items():
-        if args.serve_forms and name.split("_")[0] not in args.serve_forms.split(","):
+        if args.serve_forms and name not in args.serve_forms.split(","):
             continue
         srv = mcl.Server(budget, dtype=f["dtype"], apply=f["apply"], tol=args.serve_tol,
                          check_every=args.refine_every, max_active=f["max_active"],
@@ -558,6 +583,7 @@ def run_serve(args):
         fin = drive([0.0] * len(reqs))                 # closed loop: capacity
         t_cap = max(v[0] for v in fin.values())
         cap = len(reqs) / t_cap
+        trials = srv.trials()
         lam = args.load * cap
         gaps = np.array([r["gap"] for r in reqs]) / lam
         arr = np.cumsum(gaps) - gaps[0]
@@ -572,6 +598,8 @@ def run_serve(args):
             "all_converged": all(v[2] == 0 for v in fin.values()),
             "max_residual": float(np.nanmax([v[3] for v in fin.values()])),
             "grid": srv.grid(),
+            "batched_kernel": kernel_summary(trials, hbm_peak, hbm_src),
+            "tuner_trials": trials,
             "per_request": [[i, reqs[i]["L"], reqs[i]["m"], round(reqs[i]["ratio"], 3),
                              fin[i][1], fin[i][3], round(float(lat[i]), 4), fin[i][2]]
                             for i in range(len(reqs))]}
@@ -720,9 +748,10 @@ def main():
     ap.add_argument("--segment", type=int, default=16384,
                     help="contraction mode: sweeps between recorded contraction factors")
     ap.add_argument("--requests", type=int, default=16)
-    ap.add_argument("--serve-dtype", default="bf16", choices=["f64", "f32", "bf16"])
     ap.add_argument("--serve-tol", type=float, default=1e-10)
-    ap.add_argument("--serve-forms", default="", help="comma list of form prefixes to run")
+    ap.add_argument("--serve-forms", default="",
+                    help="comma list of forms to run (batched_bf16_coupled, batched_bf16_inverse, "
+                         "batched_f64_coupled, fp64_one_at_a_time); default all")
     ap.add_argument("--budget-gb", type=float, default=64.0)
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)

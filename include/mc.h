@@ -333,10 +333,11 @@ int mc_residual_noalloc(const double* dn, const double* loc, const double* up, i
  * (or a latched error, or maxit sweeps) are retired, their pi copied to host
  * memory and their arena memory freed.  Requests submitted between steps
  * join the next chunk.  A request's iterates are bitwise independent of the
- * other requests in the batch and of the launch grid.  With autotune = 1 the
- * first chunk of every new batch signature times candidate persistent grids
- * (1, 2, 3, 4, 6, 8 resident blocks per SM) on the live requests and keeps
- * the fastest.
+ * other requests in the batch and of every launch configuration.  With
+ * autotune = 1 the first chunks of every new batch signature time candidate
+ * configurations (persistent grid, levels per claimed unit, block-size
+ * bucketing, load depth) on the live requests and keep the fastest
+ * (mc_server_trials lists the search).
  * --------------------------------------------------------------------------- */
 typedef struct mc_server mc_server;
 
@@ -386,6 +387,32 @@ int mc_server_fetch(mc_server* server, int64_t* tag, double* pi_host, int64_t n_
 /* Launch grid in use and the number of tuned batch signatures. */
 int mc_server_grid(const mc_server* server, int32_t* blocks, int32_t* threads,
                    int32_t* n_tuned);
+
+/*
+ * One timed chunk of the autotuner (autotune = 1).  For every new batch
+ * signature the server times one live chunk per candidate configuration in a
+ * coordinate search -- the persistent grid (1, 2, 3, 4, 6, 8 resident
+ * 256-thread blocks per SM), then 2 and 4 levels per claimed unit, then the
+ * other block-size bucketing, then (low precision with blocks of m <= 64)
+ * the other load depth -- and keeps the fastest.  The paper trades block
+ * size against thread count by hand (Sect. 3); here the trade is measured on
+ * the live request mix.
+ */
+typedef struct {
+  uint64_t signature;       /* bit c set: requests of size class c present (m <= 32, 64,
+                               128, 256); bits 8..: log4 of the total level count     */
+  int32_t blocks_per_sm;    /* resident 256-thread blocks per SM of the fused launches  */
+  int32_t levels_per_unit;  /* adjacent same-parity levels per claimed unit (1, 2, 4)   */
+  int32_t split64;          /* 1: blocks of m <= 64 in a launch of their own            */
+  int32_t deep;             /* 1: 16 loads in flight per lane for low-precision m <= 64 */
+  int32_t chosen;           /* 1: the configuration kept for this signature            */
+  double chunk_ms;          /* the whole chunk (sweeps, reductions, residuals)         */
+  double sweep_ms;          /* the fused sweep launches of the chunk (CUDA events)     */
+  double sweep_bytes;       /* algorithmic bytes those launches stream                 */
+} mc_server_tuning;
+
+/* Copy up to cap timed chunks of the autotuner into out; *n = how many exist. */
+int mc_server_trials(const mc_server* server, mc_server_tuning* out, int32_t cap, int32_t* n);
 
 /* Release the server (requests still active are dropped). */
 void mc_server_destroy(mc_server* server);

@@ -29,6 +29,14 @@ class McServerDesc(ctypes.Structure):
                 ("autotune", ctypes.c_int32)]
 
 
+class McServerTuning(ctypes.Structure):
+    _fields_ = [("signature", ctypes.c_uint64), ("blocks_per_sm", ctypes.c_int32),
+                ("levels_per_unit", ctypes.c_int32), ("split64", ctypes.c_int32),
+                ("deep", ctypes.c_int32), ("chosen", ctypes.c_int32),
+                ("chunk_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double),
+                ("sweep_bytes", ctypes.c_double)]
+
+
 class McResult(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int64), ("residual_l1", ctypes.c_double),
                 ("step_l1", ctypes.c_double), ("contraction", ctypes.c_double),
@@ -87,6 +95,9 @@ def load():
     lib.mc_server_grid.argtypes = [vp, ctypes.POINTER(i32), ctypes.POINTER(i32),
                                    ctypes.POINTER(i32)]
     lib.mc_server_grid.restype = ctypes.c_int
+    lib.mc_server_trials.argtypes = [vp, ctypes.POINTER(McServerTuning), i32,
+                                     ctypes.POINTER(i32)]
+    lib.mc_server_trials.restype = ctypes.c_int
     lib.mc_server_destroy.argtypes = [vp]
     lib.mc_server_destroy.restype = None
     lib.mc_sync.argtypes = [vp]

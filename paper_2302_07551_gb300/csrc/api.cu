@@ -225,11 +225,12 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
       a.rsum = rsum;
     }
     // block Gauss-Seidel runs at most min(K, L/2) units at once (one per sweep
-    // in flight): twice that many warps keep the next diagonal claimed
+    // in flight); half as many warps again keep the next diagonal claimed
+    // without a crowd of warps spinning on later ones
     int nb = c->nb_fused;
     if (a.bgs) {
       const int64_t par = K < (L + 1) / 2 ? K : (L + 1) / 2;
-      const int64_t nbw = (2 * par + 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
+      const int64_t nbw = (par + par / 2 + 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
       if (nbw < nb) nb = (int)nbw;
     }
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));

@@ -65,9 +65,13 @@ struct mc_server {
   std::deque<Done> done;
   cudaStream_t cap;
   cudaGraphExec_t gexec;
-  BGrid g_grid;
+  BTune g_tune;          // configuration of the captured graph
   int g_chunk;
-  std::map<uint64_t, BGrid> tuned;
+  int G;                 // levels per unit of the table being built
+  std::map<uint64_t, BTune> tuned;
+  std::map<uint64_t, int> tuned_G;
+  // autotuner results: (signature, candidate, ms per chunk) of every timed chunk
+  std::vector<mc_server_tuning> trials;
   int64_t chunks;
   int32_t epoch_next;   // completion-counter base of the next chunk
 };
@@ -203,7 +207,8 @@ int begin_chunk(mc_server* s, int c) {
 
 // Chunk body on stream st: c fused sweeps (FP64) or one refinement step of c
 // fused correction sweeps (low precision), then every request's residual.
-int enqueue_chunk(mc_server* s, BGrid g, int c, cudaStream_t st) {
+// ev (optional, 2 events): recorded around the fused sweep launches.
+int enqueue_chunk(mc_server* s, BTune g, int c, cudaStream_t st, cudaEvent_t* ev = nullptr) {
   const bool lp = s->d.dtype != MC_F64;
   const int coupled = s->d.apply == MC_APPLY_COUPLED;
   if (cudaMemcpyAsync(s->t_dev, s->t_host, sizeof(BTable), cudaMemcpyHostToDevice, st) !=
@@ -211,13 +216,21 @@ int enqueue_chunk(mc_server* s, BGrid g, int c, cudaStream_t st) {
       cudaMemsetAsync(s->out_dev, 0, sizeof(BOut) * kMaxReq, st) != cudaSuccess)
     return MC_ERR_CUDA;
   unsigned long long* claim = &s->t_dev->claim[0];
+  if (lp && b_lp_zero(s->t_dev, g, st) != cudaSuccess) return MC_ERR_CUDA;
+  if (ev && cudaEventRecord(ev[0], st) != cudaSuccess) return MC_ERR_CUDA;
   if (lp) {
-    if (b_lp_step(s->t_dev, claim, s->out_dev, s->d.dtype == MC_BF16, coupled, c, g, st) !=
+    if (b_lp_sweeps(s->t_dev, claim, s->out_dev, s->d.dtype == MC_BF16, coupled, c, g, st) !=
         cudaSuccess)
       return MC_ERR_CUDA;
   } else {
     if (b_sweeps(s->t_dev, claim, s->out_dev, coupled, c, g, st) != cudaSuccess)
       return MC_ERR_CUDA;
+  }
+  if (ev && cudaEventRecord(ev[1], st) != cudaSuccess) return MC_ERR_CUDA;
+  if (lp) {
+    if (b_lp_finish(s->t_dev, s->out_dev, g, st) != cudaSuccess) return MC_ERR_CUDA;
+  } else {
+    if (b_sweeps_finish(s->t_dev, s->out_dev, c, g, st) != cudaSuccess) return MC_ERR_CUDA;
   }
   if (b_resid(s->t_dev, s->out_dev, lp ? 1 : 0, g, st) != cudaSuccess) return MC_ERR_CUDA;
   if (cudaMemcpyAsync(s->out_host, s->out_dev, sizeof(BOut) * kMaxReq, cudaMemcpyDeviceToHost,
@@ -226,16 +239,44 @@ int enqueue_chunk(mc_server* s, BGrid g, int c, cudaStream_t st) {
   return MC_OK;
 }
 
-// Grid autotuner: time one chunk per candidate persistent grid on the live
-// active set (real work: results do not depend on the grid) and keep the
-// fastest for this signature (buckets present, precision, size class).
+// Algorithmic bytes the fused sweep launches of one chunk stream: per level
+// and sweep the stored operator blocks once plus the neighbour vectors read
+// and the level written (FP64: 24 m^2 + 16 m inverse, 16 m^2 + 16 m coupled;
+// low precision: 2 e m^2 for the two off-diagonal blocks of e-byte entries,
+// + 4 m^2 for the FP32 inverse, + 16 m for the FP32 vectors d and q).
+double chunk_sweep_bytes(const mc_server* s, int c) {
+  const bool inv = s->d.apply == MC_APPLY_INVERSE;
+  double b = 0.0;
+  for (const Req* r : s->active) {
+    const double m = r->chain->lay.m, L = (double)r->chain->lay.L;
+    double lvl;
+    if (s->d.dtype == MC_F64) {
+      lvl = (inv ? 24.0 : 16.0) * m * m + 16.0 * m;
+    } else {
+      const double e = s->d.dtype == MC_F32 ? 4.0 : 2.0;
+      lvl = 2.0 * e * m * m + (inv ? 4.0 * m * m : 0.0) + 16.0 * m;
+    }
+    b += lvl * L * c;
+  }
+  return b;
+}
+
+// Autotuner: for each batch signature (size classes present, size class of
+// the total level count) time one live chunk per candidate configuration
+// (real work, counted as such: results do not depend on the configuration)
+// and keep the fastest.  Coordinate search: the persistent grid (1, 2, 3, 4,
+// 6, 8 resident 256-thread blocks per SM) with one level per unit, then 2
+// and 4 levels per unit, then the other bucket edge, then (low precision
+// with m <= 64 present) the other load depth.
 uint64_t signature(const mc_server* s) {
   const BTable* t = s->t_host;
   const int64_t lv = t->off_lv[t->n];
   int lg = 0;
   while ((1LL << lg) < lv && lg < 62) ++lg;
-  return ((uint64_t)(t->n_small > 0) << 0) | ((uint64_t)(t->n > t->n_small) << 1) |
-         ((uint64_t)(t->n_tiny > 0) << 2) | ((uint64_t)(lg / 2) << 8);
+  uint64_t sig = (uint64_t)(lg / 2) << 8;
+  for (int c = 0; c < kClasses; ++c)
+    if (t->cls_end[c] > (c ? t->cls_end[c - 1] : 0)) sig |= 1ull << c;
+  return sig;
 }
 
 // Factor status of newly admitted requests (one sync when there are any).
@@ -267,24 +308,26 @@ int check_fresh(mc_server* s) {
 // Fill the pinned request table from the active list (small blocks first);
 // returns the table order.
 std::vector<Req*> build_table(mc_server* s) {
-  // size classes m <= 64, 64 < m <= 128, m > 128, in that order
-  auto cls = [](const Req* r) { return r->chain->lay.m > 128 ? 2 : r->chain->lay.m > 64 ? 1 : 0; };
+  // size classes m <= 32, 64, 128, 256, in that order
+  auto cls = [](const Req* r) { return size_class(r->chain->lay.m); };
   std::stable_sort(s->active.begin(), s->active.end(),
                    [&](const Req* a, const Req* b) { return cls(a) < cls(b); });
   BTable* t = s->t_host;
   t->n = (int32_t)s->active.size();
-  t->n_small = 0;
-  t->n_tiny = 0;
+  for (int c = 0; c < kClasses; ++c) t->cls_end[c] = 0;
+  t->G = s->G;
   t->off_h1[0] = t->off_h2[0] = t->off_lv[0] = 0;
   const int p1 = s->d.stair == 1 ? 0 : 1;
+  const int64_t G = s->G;
   for (int i = 0; i < t->n; ++i) {
     const Req* r = s->active[(size_t)i];
     const int64_t L = r->chain->lay.L;
-    if (r->chain->lay.m <= 128) t->n_small = i + 1;
-    if (r->chain->lay.m <= 64) t->n_tiny = i + 1;
+    for (int c = cls(r); c < kClasses; ++c) t->cls_end[c] = i + 1;
     fill_req(s, r, &t->r[i]);
-    t->off_h1[i + 1] = t->off_h1[i] + (L - p1 + 1) / 2;
-    t->off_h2[i + 1] = t->off_h2[i] + (L - (1 - p1) + 1) / 2;
+    // units: groups of G levels of each half-sweep
+    const int64_t P1 = (L - p1 + 1) / 2, P2 = (L - (1 - p1) + 1) / 2;
+    t->off_h1[i + 1] = t->off_h1[i] + (P1 + G - 1) / G;
+    t->off_h2[i + 1] = t->off_h2[i] + (P2 + G - 1) / G;
     t->off_lv[i + 1] = t->off_lv[i] + L;
   }
   return std::vector<Req*>(s->active.begin(), s->active.end());
@@ -358,7 +401,8 @@ int mc_server_create(const mc_server_desc* desc, void* arena, size_t arena_bytes
     return MC_ERR_CUDA;
   }
   memset(s->t_host, 0, sizeof(BTable));
-  s->g_grid = BGrid{2 * s->num_sms, 256};
+  s->g_tune = BTune{2 * s->num_sms, 256, desc->dtype != MC_F64 ? 1 : 0, 0};
+  s->G = 1;
   *out = s;
   return MC_OK;
 }
@@ -436,45 +480,85 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
   int rc = check_fresh(s);
   if (rc != MC_OK) return rc;
   if (!s->active.empty()) {
+    const bool lp = s->d.dtype != MC_F64;
+    s->G = 1;
     std::vector<Req*> order = build_table(s);
     const uint64_t sig = signature(s);
     auto it = s->tuned.find(sig);
     if (it == s->tuned.end() && s->d.autotune) {
-      // candidates: 1, 2, 3, 4, 6, 8 resident 256-thread blocks per SM (the
-      // low-precision kernels of small blocks have the registers for 8);
-      // each runs one full chunk on the live set (real work, counted as
-      // such); tuning of this signature ends early when the active set changes
-      float best = 1e30f;
-      BGrid bestg = s->g_grid;
-      cudaEvent_t e0 = nullptr, e1 = nullptr;
-      if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-        return MC_ERR_CUDA;
-      static const int kCand[] = {1, 2, 3, 4, 6, 8};
-      for (int ci = 0; ci < 6 && rc == MC_OK; ++ci) {
-        const int k = kCand[ci];
-        const BGrid gk{k * s->num_sms, 256};
-        if (cudaEventRecord(e0, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
-        if (rc == MC_OK) rc = begin_chunk(s, c);
-        if (rc == MC_OK) rc = enqueue_chunk(s, gk, c, s->user);
-        if (rc == MC_OK && cudaEventRecord(e1, s->user) != cudaSuccess) rc = MC_ERR_CUDA;
-        if (rc == MC_OK && cudaEventSynchronize(e1) != cudaSuccess) rc = MC_ERR_CUDA;
-        float ms = 0.0f;
-        if (rc == MC_OK && cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) rc = MC_ERR_CUDA;
-        if (rc != MC_OK) break;
-        if (ms < best) {
-          best = ms;
-          bestg = gk;
+      // candidate list: grids first (G = 1, default edges and depth), then
+      // the other knobs around the best so far
+      const BTune base{2 * s->num_sms, 256, lp ? 1 : 0, 0};
+      BTune best = base;
+      int bestG = 1;
+      float best_ms = 1e30f;
+      cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+      for (cudaEvent_t& e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) return MC_ERR_CUDA;
+      const bool small_lp = lp && (sig & 3ull) != 0;
+      static const int kGrid[] = {1, 2, 3, 4, 6, 8};
+      bool stop = false;
+      for (int stage = 0; stage < 4 && !stop && rc == MC_OK; ++stage) {
+        const int ncand = stage == 0 ? 6 : stage == 1 ? 2 : (stage == 3 && !small_lp) ? 0 : 1;
+        for (int ci = 0; ci < ncand && !stop && rc == MC_OK; ++ci) {
+          BTune g = best;
+          int G = bestG;
+          if (stage == 0) g.blocks = kGrid[ci] * s->num_sms;
+          if (stage == 1) G = ci == 0 ? 2 : 4;
+          if (stage == 2) g.split64 = 1 - best.split64;
+          if (stage == 3) g.deep = 1 - best.deep;
+          s->G = G;
+          order = build_table(s);
+          if (cudaEventRecord(ev[0], s->user) != cudaSuccess) rc = MC_ERR_CUDA;
+          if (rc == MC_OK) rc = begin_chunk(s, c);
+          if (rc == MC_OK) rc = enqueue_chunk(s, g, c, s->user, ev + 1);
+          if (rc == MC_OK && cudaEventRecord(ev[3], s->user) != cudaSuccess) rc = MC_ERR_CUDA;
+          if (rc == MC_OK && cudaEventSynchronize(ev[3]) != cudaSuccess) rc = MC_ERR_CUDA;
+          float ms = 0.0f, sw = 0.0f;
+          if (rc == MC_OK && (cudaEventElapsedTime(&ms, ev[0], ev[3]) != cudaSuccess ||
+                              cudaEventElapsedTime(&sw, ev[1], ev[2]) != cudaSuccess))
+            rc = MC_ERR_CUDA;
+          if (rc != MC_OK) break;
+          mc_server_tuning tr{};
+          tr.signature = sig;
+          tr.blocks_per_sm = g.blocks / s->num_sms;
+          tr.levels_per_unit = G;
+          tr.split64 = g.split64;
+          tr.deep = g.deep;
+          tr.chunk_ms = ms;
+          tr.sweep_ms = sw;
+          tr.sweep_bytes = chunk_sweep_bytes(s, c);
+          s->trials.push_back(tr);
+          if (ms < best_ms) {
+            best_ms = ms;
+            best = g;
+            bestG = G;
+          }
+          stop = process_outputs(s, order, c) > 0 || s->active.empty();
         }
-        if (process_outputs(s, order, c) > 0 || s->active.empty()) break;
       }
-      cudaEventDestroy(e0);
-      cudaEventDestroy(e1);
+      for (cudaEvent_t e : ev) cudaEventDestroy(e);
       if (rc != MC_OK) return rc;
-      s->tuned[sig] = bestg;
+      s->tuned[sig] = best;
+      s->tuned_G[sig] = bestG;
+      for (mc_server_tuning& tr : s->trials)
+        if (tr.signature == sig)
+          tr.chosen = tr.blocks_per_sm == best.blocks / s->num_sms && tr.levels_per_unit == bestG &&
+                      tr.split64 == best.split64 && tr.deep == best.deep;
     } else {
-      const BGrid g = it != s->tuned.end() ? it->second : s->g_grid;
-      if (!s->gexec || s->g_chunk != c || s->g_grid.blocks != g.blocks ||
-          s->g_grid.threads != g.threads) {
+      BTune g{2 * s->num_sms, 256, lp ? 1 : 0, 0};
+      int G = 1;
+      if (it != s->tuned.end()) {
+        g = it->second;
+        G = s->tuned_G[sig];
+      }
+      if (G != s->G) {
+        s->G = G;
+        order = build_table(s);
+      }
+      if (!s->gexec || s->g_chunk != c || s->g_tune.blocks != g.blocks ||
+          s->g_tune.threads != g.threads || s->g_tune.split64 != g.split64 ||
+          s->g_tune.deep != g.deep) {
         if (s->gexec) {
           cudaGraphExecDestroy(s->gexec);
           s->gexec = nullptr;
@@ -496,7 +580,7 @@ int mc_server_step(mc_server* s, int32_t* n_active, int32_t* n_done) {
           return MC_ERR_CUDA;
         }
         s->g_chunk = c;
-        s->g_grid = g;
+        s->g_tune = g;
       }
       rc = begin_chunk(s, c);
       if (rc != MC_OK) return rc;
@@ -527,9 +611,17 @@ int mc_server_fetch(mc_server* s, int64_t* tag, double* pi_host, int64_t n_cap, 
 
 int mc_server_grid(const mc_server* s, int32_t* blocks, int32_t* threads, int32_t* n_tuned) {
   if (!s) return MC_ERR_ARG;
-  if (blocks) *blocks = s->g_grid.blocks;
-  if (threads) *threads = s->g_grid.threads;
+  if (blocks) *blocks = s->g_tune.blocks;
+  if (threads) *threads = s->g_tune.threads;
   if (n_tuned) *n_tuned = (int32_t)s->tuned.size();
+  return MC_OK;
+}
+
+int mc_server_trials(const mc_server* s, mc_server_tuning* out, int32_t cap, int32_t* n) {
+  if (!s || cap < 0 || (cap > 0 && !out)) return MC_ERR_ARG;
+  const int32_t total = (int32_t)s->trials.size();
+  for (int32_t i = 0; i < total && i < cap; ++i) out[i] = s->trials[(size_t)i];
+  if (n) *n = total;
   return MC_OK;
 }
 

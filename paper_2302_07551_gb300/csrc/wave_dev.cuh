@@ -21,6 +21,22 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   return v;
 }
 
+// Polling load: relaxed (no ordering, no L1 invalidation as an acquire at
+// GPU scope would do on every poll); the acquire follows once the value is
+// ready.
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Back-off between polls: 128 ns doubling to 2 us, so that many waiting warps
+// do not flood L2 with polls while the units they wait for run.
+__device__ __forceinline__ unsigned backoff(unsigned ns) {
+  __nanosleep(ns);
+  return ns < 2048u ? 2u * ns : ns;
+}
+
 __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
@@ -33,18 +49,19 @@ __device__ __forceinline__ unsigned long long global_ns() {
 
 // Wait until levels l-1 and l+1 (where they exist) have completed `need`
 // writes, for at most wait_ns nanoseconds (then MC_ERR_TIMEOUT is latched in
-// *status unless it holds an earlier error).  Lane 0 polls; then
-// every lane performs its own acquire of both counters, which orders its
-// reads of the neighbour vectors after the producers' writes.
+// *status unless it holds an earlier error).  Lane 0 polls with relaxed
+// loads; then every lane performs its own acquire of both counters, which
+// orders its reads of the neighbour vectors after the producers' writes.
 __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64_t L, int need,
                                                 int* status, int lane,
                                                 unsigned long long wait_ns) {
   const bool lo = l > 0, up = l < L - 1;
   if (lane == 0) {
     unsigned long long t0 = 0;
+    unsigned ns = 128;
     for (int it = 0;; ++it) {
-      const bool ok = (!lo || ld_acquire(ver + l - 1) >= need) &&
-                      (!up || ld_acquire(ver + l + 1) >= need);
+      const bool ok = (!lo || ld_relaxed(ver + l - 1) >= need) &&
+                      (!up || ld_relaxed(ver + l + 1) >= need);
       if (ok) break;
       if (it == 0) {
         t0 = global_ns();
@@ -52,7 +69,7 @@ __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64
         atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(128);
+      ns = backoff(ns);
     }
   }
   __syncwarp();
@@ -68,9 +85,10 @@ __device__ __forceinline__ void wait_neighbours2(const int* ver, int64_t l, int6
   const bool lo = l > 0 && need_lo > 0, up = l < L - 1 && need_up > 0;
   if (lane == 0) {
     unsigned long long t0 = 0;
+    unsigned ns = 128;
     for (int it = 0;; ++it) {
-      const bool ok = (!lo || ld_acquire(ver + l - 1) >= need_lo) &&
-                      (!up || ld_acquire(ver + l + 1) >= need_up);
+      const bool ok = (!lo || ld_relaxed(ver + l - 1) >= need_lo) &&
+                      (!up || ld_relaxed(ver + l + 1) >= need_up);
       if (ok) break;
       if (it == 0) {
         t0 = global_ns();
@@ -78,7 +96,7 @@ __device__ __forceinline__ void wait_neighbours2(const int* ver, int64_t l, int6
         atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
         break;
       }
-      __nanosleep(128);
+      ns = backoff(ns);
     }
   }
   __syncwarp();
@@ -131,12 +149,13 @@ __device__ __forceinline__ void wait_band(const int* ver, int64_t l, int64_t L, 
   const int64_t j = l - bw + lane;
   const bool mine = lane <= 2 * bw && j >= 0 && j < L;
   const int nj = (j == l - 1 || j == l + 1) ? near_need : need;
-  bool ok = !mine || ld_acquire(ver + j) >= nj;
+  bool ok = !mine || ld_relaxed(ver + j) >= nj;
   if (!__all_sync(0xffffffffu, ok)) {
     const unsigned long long t0 = global_ns();
+    unsigned ns = 128;
     while (true) {
-      __nanosleep(128);
-      if (!ok) ok = ld_acquire(ver + j) >= nj;
+      ns = backoff(ns);
+      if (!ok) ok = ld_relaxed(ver + j) >= nj;
       if (__all_sync(0xffffffffu, ok)) break;
       if (__any_sync(0xffffffffu, global_ns() - t0 > wait_ns)) {
         if (lane == 0) atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
@@ -146,6 +165,45 @@ __device__ __forceinline__ void wait_band(const int* ver, int64_t l, int64_t L, 
   }
   for (int64_t i = l - bw; i <= l + bw; ++i)
     if (i >= 0 && i < L) (void)ld_acquire(ver + i);
+}
+
+// Wait until the `count` (<= 32) levels first, first + stride, ... (those in
+// [0, L)) have completed `need` writes; lane i polls level first + stride i.
+// Afterwards every lane acquires all of them itself.  Bounded like
+// wait_neighbours.
+__device__ __forceinline__ void wait_levels(const int* ver, int64_t first, int stride, int count,
+                                            int64_t L, int need, int* status, int lane,
+                                            unsigned long long wait_ns) {
+  const int64_t j = first + (int64_t)stride * lane;
+  const bool mine = lane < count && j >= 0 && j < L;
+  bool ok = !mine || ld_relaxed(ver + j) >= need;
+  if (!__all_sync(0xffffffffu, ok)) {
+    const unsigned long long t0 = global_ns();
+    unsigned ns = 128;
+    while (true) {
+      ns = backoff(ns);
+      if (!ok) ok = ld_relaxed(ver + j) >= need;
+      if (__all_sync(0xffffffffu, ok)) break;
+      if (__any_sync(0xffffffffu, global_ns() - t0 > wait_ns)) {
+        if (lane == 0) atomicCAS(status, 0, (int)MC_ERR_TIMEOUT);
+        break;
+      }
+    }
+  }
+  for (int i = 0; i < count; ++i) {
+    const int64_t jj = first + (int64_t)stride * i;
+    if (jj >= 0 && jj < L) (void)ld_acquire(ver + jj);
+  }
+}
+
+// Levels first, first + stride, ... (count <= 32) now hold version v: every
+// lane's stores are made visible before lane i releases level
+// first + stride i.
+__device__ __forceinline__ void publish_levels(int* ver, int64_t first, int stride, int count,
+                                               int v, int lane) {
+  __threadfence();
+  __syncwarp();
+  if (lane < count) st_release(ver + first + (int64_t)stride * lane, v);
 }
 
 // Level l now holds its version v: every lane's stores of z_l are made

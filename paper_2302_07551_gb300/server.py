@@ -80,6 +80,22 @@ class Server:
                                            ctypes.byref(n)), "mc_server_grid")
         return b.value, t.value, n.value
 
+    def trials(self):
+        """The autotuner's timed chunks: one dict per candidate configuration
+        (signature, blocks per SM, levels per unit, bucketing, load depth,
+        whether it was kept, chunk and sweep-launch milliseconds, algorithmic
+        bytes of the sweep launches)."""
+        n = ctypes.c_int32()
+        nat.check(self._lib.mc_server_trials(self._h, None, 0, ctypes.byref(n)),
+                  "mc_server_trials")
+        arr = (nat.McServerTuning * max(n.value, 1))()
+        nat.check(self._lib.mc_server_trials(self._h, arr, n.value, ctypes.byref(n)),
+                  "mc_server_trials")
+        return [dict(signature=t.signature, blocks_per_sm=t.blocks_per_sm,
+                     levels_per_unit=t.levels_per_unit, split64=t.split64, deep=t.deep,
+                     chosen=bool(t.chosen), chunk_ms=t.chunk_ms, sweep_ms=t.sweep_ms,
+                     sweep_bytes=t.sweep_bytes) for t in arr[:n.value]]
+
     def run_until_idle(self):
         """Step until no request is active; returns all finished results."""
         out = []

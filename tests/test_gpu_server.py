@@ -125,3 +125,40 @@ def test_bad_request_is_isolated():
     ref = oracle.Chain(*good).solve(tol=1e-13, maxit=200000, check_every=32)["x"]
     assert rel_l1(out[1][0], ref) <= 1e-10
     srv.close()
+
+
+@pytest.mark.parametrize("dtype", ["f64", "bf16"])
+def test_autotuner_search_space_and_invariance(dtype):
+    """The autotuner times live chunks over the persistent grid, the levels per
+    claimed unit (1, 2, 4), the block-size bucketing and (low precision, small
+    blocks) the load depth, keeps one configuration per batch signature, and
+    none of them changes a result: every request's pi is bitwise the one of an
+    untuned server, and matches the oracle."""
+    mix = [(300, 16, 0.6), (257, 32, 0.8), (200, 64, 0.7), (120, 128, 0.9), (90, 64, 0.5)]
+    out = {}
+    for tune in (False, True):
+        srv = mc.Server(2 << 30, dtype=dtype, tol=1e-11, check_every=16, autotune=tune)
+        for i, (L, m, ratio) in enumerate(mix):
+            assert srv.submit(i, *blocks_for(40 + i, L, m, ratio))
+        out[tune] = {t: (pi, r, st) for t, pi, r, st in srv.run_until_idle()}
+        if tune:
+            tr = srv.trials()
+            assert {t["levels_per_unit"] for t in tr} >= {1, 2, 4}
+            assert {t["split64"] for t in tr} == {0, 1}
+            assert {t["blocks_per_sm"] for t in tr} >= {1, 2, 3, 4, 6, 8}
+            if dtype != "f64":
+                assert {t["deep"] for t in tr} == {0, 1}
+            sigs = {t["signature"] for t in tr}
+            for sg in sigs:
+                assert sum(t["chosen"] for t in tr if t["signature"] == sg) == 1
+            assert all(t["sweep_ms"] > 0 and t["sweep_bytes"] > 0 and t["chunk_ms"] >= t["sweep_ms"]
+                       for t in tr)
+        srv.close()
+    for i, (L, m, ratio) in enumerate(mix):
+        pi_t, r_t, st_t = out[True][i]
+        pi_u, r_u, st_u = out[False][i]
+        assert st_t == st_u == 0 and r_t["sweeps"] == r_u["sweeps"]
+        assert np.array_equal(pi_t, pi_u), i
+        ref = oracle.Chain(*blocks_for(40 + i, L, m, ratio)).solve(
+            tol=1e-13, maxit=400000, check_every=64)["x"]
+        assert rel_l1(pi_t, ref) <= 1e-10, i
