@@ -269,10 +269,11 @@ __global__ void __launch_bounds__(256) k_b_zero_d(const BTable* __restrict__ t) 
 
 // Low-precision correction sweeps of one bucket (size classes [c0, c1)), all
 // K sweeps of a refinement step in one launch, d in place.  Paths by the
-// bucket's largest block: CLS 0 -> m <= 64 (16-byte lane loads, BW loads in
-// flight, several lanes per column), CLS 1 -> m <= 128 (G = GF = 2: FP32 or
-// two-row BF16), CLS 2 -> m <= 256 (FP32 G = 4, four-row BF16 G = 2; GF = 4);
-// one kernel per path, so that each has the register count of its own code.
+// request's block size: m <= 64 -> 16-byte lane loads, BW loads in flight,
+// several lanes per column; 64 < m <= 128 -> G = GF = 2 (FP32 or two-row
+// BF16); m > 128 -> FP32 G = 4, four-row BF16 G = 2, GF = 4.  CLS bounds the
+// paths a kernel holds (0: m <= 64, 1: m <= 128, 2: m > 128), so that each
+// kernel has the register count of its largest path.
 template <typename TS, typename TL, bool COUPLED, int CLS, int BW>
 __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ t, int K, int c0,
                                                      int c1, unsigned long long* claim,
@@ -301,12 +302,14 @@ __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ 
                   &out[u.r].status, lane, kWaitNs);
     for (int i = 0; i < u.n; ++i) {
       const int64_t l = u.l + 2 * i;
+      // the path follows the request's m alone (never the bucket), so every
+      // bucketing computes a level with the same arithmetic
       if constexpr (CLS == 2) {
         constexpr int GL = Pack<TL>::V == 2 ? 4 : 2;
         level_sweep_lp<TL, GL, 4, COUPLED, true>((const TL*)Q->lA, (const TL*)Q->lB, Q->lC,
                                                  Q->sc, Q->d, Q->q, l, Q->L, Q->m, Q->lp_bs,
                                                  Q->lp_cbs, slice, lane);
-      } else if constexpr (CLS == 1) {
+      } else if (CLS == 1 && Q->m > 64) {
         level_sweep_lp<TS, 2, 2, COUPLED, true>((const TS*)Q->lA, (const TS*)Q->lB, Q->lC,
                                                 Q->sc, Q->d, Q->q, l, Q->L, Q->m, Q->lp_bs,
                                                 Q->lp_cbs, slice, lane);
