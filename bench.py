@@ -263,6 +263,12 @@ def run_mine(args):
 
     x = torch.full((N,), 1.0 / N, dtype=torch.float64, device=dev)
     y = torch.empty_like(x)
+    # set-up (untimed): the library's autotuner picks the fused launches'
+    # blocks per SM (and, for low-precision storage, levels per unit)
+    tuning = None
+    if not args.no_tune:
+        bps, lpu, tms = ch.tune(x, min(64, args.steps, 1024))
+        tuning = {"blocks_per_sm": bps, "levels_per_unit": lpu, "tuned_ms": tms}
     torch.cuda.synchronize()
     sampler = ClockSampler(gpu_id(local))
     sampler.start()
@@ -428,6 +434,7 @@ def run_mine(args):
         "data": "synthetic (seeded QBD generator, level-dependent blocks)",
         "config": {"workload": name, "L": L, "m": m, "N": N, "apply": args.apply, "stair": 1,
                    "check_every": check if args.dtype == "f64" else None,
+                   "tuning": tuning,
                    "paired_zero_quadrants_skipped": bool(paired),
                    "block_bytes": sweep_bytes - 16 * N,
                    "refine_every": args.refine_every if args.dtype != "f64" else None,
@@ -756,6 +763,8 @@ def main():
     ap.add_argument("--load", type=float, default=0.8)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the default launch configuration (skip mc_tune at set-up)")
     ap.add_argument("--measure-fp64-peak", action="store_true")
     args = ap.parse_args()
     if args.measure_fp64_peak:

@@ -209,7 +209,8 @@ int mc_sweep(mc_chain* chain, const double* x_in, double* x_out, int64_t nsweeps
 /*
  * As mc_sweep but with HOST vectors (pinned memory recommended): returns the
  * result in x_out_host and the stats of mc_sweep (3 doubles, residual
- * included; NULL: no stats and no residual) in stats_host.  Stair chains
+ * included; NULL: no stats, and neither the residual nor the step error is
+ * formed, so the input is not read a second time) in stats_host.  Stair chains
  * read a page-locked x_in_host (cudaHostAlloc / cudaHostRegister) in place
  * from the kernels over the CPU-GPU link, and when x_out_host is page-locked
  * and the sweeps run as one fused launch, the normalisation stores the
@@ -416,6 +417,40 @@ int mc_server_trials(const mc_server* server, mc_server_tuning* out, int32_t cap
 
 /* Release the server (requests still active are dropped). */
 void mc_server_destroy(mc_server* server);
+
+/*
+ * Launch configuration of a chain's fused persistent launches: the trade
+ * between block size and parallelism that the paper tunes by hand (Sect. 3),
+ * chosen here by measurement.
+ *   blocks_per_sm: resident 256-thread blocks per SM (0: all the kernel's
+ *     occupancy allows, the default);
+ *   levels_per_unit: adjacent same-parity levels per claimed work unit of the
+ *     low-precision correction sweeps (1, 2 or 4; one claim, one neighbour
+ *     wait and one completion fence per unit); FP64 sweeps use 1.
+ * Neither changes any result: every level is computed the same way.
+ */
+typedef struct {
+  int32_t blocks_per_sm;
+  int32_t levels_per_unit;
+} mc_tuning;
+
+/* Set the configuration (MC_ERR_ARG for values outside the ranges above). */
+int mc_set_tuning(mc_chain* chain, const mc_tuning* tuning);
+int mc_get_tuning(const mc_chain* chain, mc_tuning* tuning);
+
+/*
+ * Autotune the chain: time nsweeps (1..1024) fused sweeps from the device
+ * vector x (FP64 chains: stair or block Gauss-Seidel sweeps with their
+ * residual units, blocks_per_sm in {0, 1, 2}; low-precision chains: the
+ * correction sweeps of one refinement step from x, blocks_per_sm in
+ * {0, 2, 3, 4} x levels_per_unit in {1, 2, 4}), each candidate once to warm up
+ * and once timed with CUDA events, and keep the fastest.  x is only read;
+ * the chain's scratch vectors are overwritten.  best, best_ms (may be NULL)
+ * receive the choice and its time.  Syncs.  Errors: MC_ERR_ARG,
+ * MC_ERR_NOT_FACTORED, MC_ERR_CUDA.
+ */
+int mc_tune(mc_chain* chain, const double* x, int64_t nsweeps, mc_tuning* best,
+            double* best_ms);
 
 /* Wait for the handle's stream and return (and clear) the device status. */
 int mc_sync(mc_chain* chain);

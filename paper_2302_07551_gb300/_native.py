@@ -37,6 +37,10 @@ class McServerTuning(ctypes.Structure):
                 ("sweep_bytes", ctypes.c_double)]
 
 
+class McTuning(ctypes.Structure):
+    _fields_ = [("blocks_per_sm", ctypes.c_int32), ("levels_per_unit", ctypes.c_int32)]
+
+
 class McResult(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int64), ("residual_l1", ctypes.c_double),
                 ("step_l1", ctypes.c_double), ("contraction", ctypes.c_double),
@@ -100,6 +104,12 @@ def load():
     lib.mc_server_trials.restype = ctypes.c_int
     lib.mc_server_destroy.argtypes = [vp]
     lib.mc_server_destroy.restype = None
+    lib.mc_set_tuning.argtypes = [vp, ctypes.POINTER(McTuning)]
+    lib.mc_set_tuning.restype = ctypes.c_int
+    lib.mc_get_tuning.argtypes = [vp, ctypes.POINTER(McTuning)]
+    lib.mc_get_tuning.restype = ctypes.c_int
+    lib.mc_tune.argtypes = [vp, vp, i64, ctypes.POINTER(McTuning), ctypes.POINTER(dbl)]
+    lib.mc_tune.restype = ctypes.c_int
     lib.mc_sync.argtypes = [vp]
     lib.mc_sync.restype = ctypes.c_int
     lib.mc_destroy.argtypes = [vp]

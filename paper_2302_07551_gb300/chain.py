@@ -151,6 +151,26 @@ class Chain:
                                       _ptr(out)), "mc_export")
         return out
 
+    def tune(self, x, nsweeps=64):
+        """mc_tune: time the fused launch configurations on nsweeps sweeps
+        from x (a CUDA float64 vector, only read) and keep the fastest;
+        returns (blocks_per_sm, levels_per_unit, milliseconds)."""
+        _need(x, (self.N,), "x")
+        t = nat.McTuning()
+        ms = ctypes.c_double()
+        nat.check(self._lib.mc_tune(self._h, _ptr(x), int(nsweeps), ctypes.byref(t),
+                                    ctypes.byref(ms)), "mc_tune")
+        return t.blocks_per_sm, t.levels_per_unit, ms.value
+
+    def set_tuning(self, blocks_per_sm=0, levels_per_unit=1):
+        nat.check(self._lib.mc_set_tuning(self._h, ctypes.byref(
+            nat.McTuning(int(blocks_per_sm), int(levels_per_unit)))), "mc_set_tuning")
+
+    def tuning(self):
+        t = nat.McTuning()
+        nat.check(self._lib.mc_get_tuning(self._h, ctypes.byref(t)), "mc_get_tuning")
+        return t.blocks_per_sm, t.levels_per_unit
+
     def sync(self):
         nat.check(self._lib.mc_sync(self._h), "mc_sync")
 

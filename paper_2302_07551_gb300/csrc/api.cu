@@ -176,7 +176,7 @@ static bool split_resid_ok(const mc_chain* c) { return c->d.stair <= 2 && c->lay
 // after its scale reduction, after the last normalisation.
 static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int64_t n,
                                 double* stats_out, cudaStream_t s, cudaEvent_t* ev,
-                                bool resid) {
+                                bool resid, bool step) {
   const bool coupled = c->d.apply == MC_APPLY_COUPLED;
   const size_t pe = c->lay.plane_bytes / sizeof(double);
   const int64_t L = c->lay.L;
@@ -228,6 +228,7 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     // in flight); half as many warps again keep the next diagonal claimed
     // without a crowd of warps spinning on later ones
     int nb = c->nb_fused;
+    if (c->tune_bps > 0 && c->tune_bps * c->num_sms < nb) nb = c->tune_bps * c->num_sms;
     if (a.bgs) {
       const int64_t par = K < (L + 1) / 2 ? K : (L + 1) / 2;
       const int64_t nbw = (par + par / 2 + 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
@@ -247,7 +248,7 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
     const double* last = banded ? ((K & 1) ? c->xb : c->z) : c->z;
     const double* prev = banded ? ((K & 1) ? c->z : c->xb) : c->xb;
     nn.z = last;
-    nn.x_old = final ? (K == 1 ? in : prev) : nullptr;
+    nn.x_old = (final && step) ? (K == 1 ? in : prev) : nullptr;
     nn.s_old = scale + 1;
     nn.x_new = dst;
     nn.s = scale;
@@ -266,11 +267,12 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
 // nsweeps sweeps src -> dst (in place allowed).  Stair splittings run as
 // fused launches; the comparison splittings one sweep at a time, each
 // normalised.  resid: form ||Q^T dst||_1 from the splitting (stats[2]) where
-// split_resid_ok.
+// split_resid_ok.  step = false: a fused call skips the step error of its
+// last sweep (stats[1] = 0) and never reads the previous iterate again.
 static int enqueue_sweeps(mc_chain* c, const double* src, double* dst, int64_t n,
                           double* stats_out, cudaStream_t s, cudaEvent_t* ev = nullptr,
-                          bool resid = false) {
-  if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev, resid);
+                          bool resid = false, bool step = true) {
+  if (fused_ok(c)) return enqueue_sweeps_fused(c, src, dst, n, stats_out, s, ev, resid, step);
   for (int64_t k = 0; k < n; ++k) {
     const int rc = enqueue_sweep(c, k == 0 ? src : dst, dst, k == n - 1 ? stats_out : nullptr, s,
                                  ev ? ev + 4 * k : nullptr);
@@ -319,7 +321,7 @@ static int enqueue_lp_sweeps_fused(mc_chain* c, int64_t K, cudaStream_t s) {
   CK(launch_sweeps_lp(lpA(c), lpB(c), lpC(c), lpSc(c), lpD(c), lpQ(c), c->lay.L, c->lay.m,
                       c->d.stair == 1 ? 0 : 1, c->lay.lp_bs, c->lay.lp_cbs, c->lay.lp == 2,
                       c->d.apply == MC_APPLY_COUPLED, K, c->fver, c->fclaim, c->hdr, kFusedWaitNs,
-                      c->num_sms, s));
+                      c->num_sms, c->tune_lpu, c->tune_bps, s));
   return MC_OK;
 }
 
@@ -413,6 +415,8 @@ int mc::chain_init(const mc_desc* desc, void* workspace, size_t ws_bytes, cudaSt
   int64_t wf = wps * sms;
   if (wf > lay.L) wf = lay.L;
   c->nb_fused = (int)((wf + kWarpsPerBlock - 1) / kWarpsPerBlock);
+  c->tune_bps = 0;
+  c->tune_lpu = 1;
   int64_t nbn = (lay.N + 4 * kNormThreads - 1) / (4 * kNormThreads);
   if (nbn > 8 * sms) nbn = 8 * sms;
   if (nbn > kMaxNormBlocks) nbn = kMaxNormBlocks;
@@ -640,7 +644,7 @@ int mc_sweep_host(mc_chain* c, const double* x_in_host, double* x_out_host, int6
   const bool split = split_resid_ok(c);
   double* res_dev = out_dev ? out_dev : c->xa;
   int rc = enqueue_sweeps(c, in_dev ? in_dev : c->xa, res_dev, nsweeps, nullptr, c->user, nullptr,
-                          stats_host != nullptr && split);
+                          stats_host != nullptr && split, stats_host != nullptr);
   if (rc == MC_OK && stats_host && !split) rc = enqueue_residual(c, res_dev, c->user);
   if (rc != MC_OK) return rc;
   if (!out_dev)
@@ -874,6 +878,89 @@ int mc_export(mc_chain* c, int32_t plane, int64_t level0, int64_t count, double*
   const double* src = c->planes + plane * pe + (size_t)level0 * c->lay.ms;
   CK(cudaMemcpy2DAsync(dst_dev, mm * sizeof(double), src, (size_t)c->lay.ms * sizeof(double),
                        mm * sizeof(double), (size_t)count, cudaMemcpyDeviceToDevice, c->user));
+  return MC_OK;
+}
+
+int mc_set_tuning(mc_chain* c, const mc_tuning* t) {
+  if (!c || !t || t->blocks_per_sm < 0 || t->blocks_per_sm > 16 ||
+      (t->levels_per_unit != 1 && t->levels_per_unit != 2 && t->levels_per_unit != 4) ||
+      (!c->lay.lp && t->levels_per_unit != 1))
+    return MC_ERR_ARG;
+  c->tune_bps = t->blocks_per_sm;
+  c->tune_lpu = t->levels_per_unit;
+  return MC_OK;
+}
+
+int mc_get_tuning(const mc_chain* c, mc_tuning* t) {
+  if (!c || !t) return MC_ERR_ARG;
+  t->blocks_per_sm = c->tune_bps;
+  t->levels_per_unit = c->tune_lpu;
+  return MC_OK;
+}
+
+int mc_tune(mc_chain* c, const double* x, int64_t nsweeps, mc_tuning* best, double* best_ms) {
+  if (!c || !x || ((uintptr_t)x & 7u) || nsweeps < 1 || nsweeps > kMaxFusedSweeps)
+    return MC_ERR_ARG;
+  if (!c->factored) return MC_ERR_NOT_FACTORED;
+  if (!c->lay.lp && !fused_ok(c)) return MC_ERR_ARG;
+  const int64_t N = c->lay.N;
+  // candidates: blocks per SM (0 = the kernel's occupancy) x levels per unit
+  static const int kBpsF64[] = {0, 1, 2};
+  static const int kBpsLp[] = {0, 2, 3, 4};
+  static const int kLpu[] = {1, 2, 4};
+  const int nb = c->lay.lp ? 4 : 3, nl = c->lay.lp ? 3 : 1;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return MC_ERR_CUDA;
+  }
+  const int bps0 = c->tune_bps, lpu0 = c->tune_lpu;
+  int rc = MC_OK;
+  // low precision: the correction sweeps of one refinement step from x (r and
+  // q of x, d from zero); FP64: the fused sweeps from x into the scratch
+  // iterate, with the residual units of a solve chunk.  x is only read.
+  if (c->lay.lp) {
+    if (cudaMemcpyAsync(c->xa, x, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice,
+                        c->user) != cudaSuccess)
+      rc = MC_ERR_CUDA;
+    if (rc == MC_OK) rc = enqueue_residual(c, c->xa, c->user, lpQ(c));
+  }
+  float best_t = 1e30f;
+  mc_tuning bt{bps0, lpu0};
+  for (int bi = 0; bi < nb && rc == MC_OK; ++bi)
+    for (int li = 0; li < nl && rc == MC_OK; ++li) {
+      c->tune_bps = c->lay.lp ? kBpsLp[bi] : kBpsF64[bi];
+      c->tune_lpu = kLpu[li];
+      for (int rep = 0; rep < 2 && rc == MC_OK; ++rep) {   // the first run warms up
+        if (c->lay.lp &&
+            cudaMemsetAsync(lpD(c), 0, (size_t)N * sizeof(float), c->user) != cudaSuccess)
+          rc = MC_ERR_CUDA;
+        if (rc == MC_OK && cudaEventRecord(e0, c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+        if (rc == MC_OK)
+          rc = c->lay.lp ? enqueue_lp_sweeps_fused(c, nsweeps, c->user)
+                         : enqueue_sweeps(c, x, c->xa, nsweeps, nullptr, c->user, nullptr,
+                                          split_resid_ok(c));
+        if (rc == MC_OK && cudaEventRecord(e1, c->user) != cudaSuccess) rc = MC_ERR_CUDA;
+      }
+      float ms = 0.0f;
+      if (rc == MC_OK && (cudaEventSynchronize(e1) != cudaSuccess ||
+                          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess))
+        rc = MC_ERR_CUDA;
+      if (rc == MC_OK && ms < best_t) {
+        best_t = ms;
+        bt.blocks_per_sm = c->tune_bps;
+        bt.levels_per_unit = c->tune_lpu;
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->tune_bps = rc == MC_OK ? bt.blocks_per_sm : bps0;
+  c->tune_lpu = rc == MC_OK ? bt.levels_per_unit : lpu0;
+  if (rc != MC_OK) return rc;
+  const int st = sync_header(c);
+  if (st != MC_OK) return st;
+  if (best) *best = bt;
+  if (best_ms) *best_ms = best_t;
   return MC_OK;
 }
 

@@ -20,6 +20,8 @@ struct mc_chain {
   int* fver;                 // [L] completion counters, after the queue counter
   unsigned long long* fclaim;
   int nb_fused;              // grid of the fused multi-sweep kernel
+  int tune_bps;              // blocks per SM of the fused launches (0: default)
+  int tune_lpu;              // levels per unit of the low-precision fused launches
   cudaGraphExec_t gexec;     // cached chunk graph of mc_solve
   int g_chunk, g_resid;
 };

@@ -41,11 +41,13 @@ struct LpArgs {
 };
 
 // All `K` correction sweeps of one refinement step in one persistent launch:
-// units (sweep k, half-sweep h, level l) claimed in order, each waiting for
-// its neighbour levels through per-level completion counters (as the FP64
-// fused sweeps).  d is updated in place; a unit overwrites level l only after
-// the units that read its previous value (its neighbours' previous updates)
-// have completed, which is the condition it waits for.
+// units (sweep k, half-sweep h, levels l0, l0 + 2, ..., at most lpu adjacent
+// levels of the half-sweep) claimed in order, each waiting for its
+// neighbour levels through per-level completion counters (as the FP64 fused
+// sweeps): one claim, one wait for the lpu + 1 neighbours and one completion
+// fence per unit.  d is updated in place; a unit overwrites its levels only
+// after the units that read their previous values (the neighbours' previous
+// updates) have completed, which is the condition it waits for.
 template <typename T>
 struct SmallOf {
   using type = unsigned short;   // BF16 bits
@@ -58,7 +60,7 @@ struct SmallOf<float> {
 // SMALL = 16, 32 or 64: blocks of at most SMALL rows through
 // level_sweep_lp_small; 0: level_sweep_lp.
 template <typename T, int G, int GF, bool COUPLED, int SMALL = 0>
-__global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver,
+__global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int lpu, int* ver,
                                                    unsigned long long* claim, Header* hdr,
                                                    unsigned long long wait_ns) {
   extern __shared__ float fsh[];
@@ -68,17 +70,25 @@ __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver
   const T* Ap = reinterpret_cast<const T*>(a.A);
   const T* Bp = reinterpret_cast<const T*>(a.B);
   const int64_t P0 = (a.L - a.parity + 1) / 2;   // levels of half-sweep 1
-  const unsigned long long total = (unsigned long long)K * (unsigned long long)a.L;
+  const int64_t P1 = a.L - P0;
+  const int64_t U0 = (P0 + lpu - 1) / lpu, U1 = (P1 + lpu - 1) / lpu;   // units per half-sweep
+  const unsigned long long per = (unsigned long long)(U0 + U1);
+  const unsigned long long total = (unsigned long long)K * per;
   unsigned long long q0 = claim_unit(claim, lane);
   unsigned long long q = __shfl_sync(0xffffffffu, q0, 0);
   while (q < total) {
     q0 = claim_unit(claim, lane);
-    const int64_t k = (int64_t)(q / (unsigned long long)a.L);
-    const int64_t r = (int64_t)q - k * a.L;
-    const bool h2 = r >= P0;
-    const int64_t l = h2 ? 2 * (r - P0) + (1 - a.parity) : 2 * r + a.parity;
+    const int64_t k = (int64_t)(q / per);
+    const int64_t r = (int64_t)q - k * (int64_t)per;
+    const bool h2 = r >= U0;
+    const int64_t g = h2 ? r - U0 : r;
+    const int64_t l0 = 2 * lpu * g + (h2 ? 1 - a.parity : a.parity);
+    const int64_t left = (h2 ? P1 : P0) - (int64_t)lpu * g;
+    const int n = left < lpu ? (int)left : lpu;
     const int need = (int)(h2 ? k + 1 : k);
-    if (need > 0) wait_neighbours(ver, l, a.L, need, &hdr->status, lane, wait_ns);
+    if (need > 0) wait_levels(ver, l0 - 1, 2, n + 1, a.L, need, &hdr->status, lane, wait_ns);
+    for (int i = 0; i < n; ++i) {
+    const int64_t l = l0 + 2 * i;
     if constexpr (SMALL > 0) {
       using S = typename SmallOf<T>::type;
       // BF16: 16 loads in flight (single chains; the batched kernel keeps 8,
@@ -92,7 +102,8 @@ __global__ void __launch_bounds__(256) k_sweeps_lp(LpArgs a, int64_t K, int* ver
       level_sweep_lp<T, G, GF, COUPLED, true>(Ap, Bp, a.C, a.sc, a.d, a.q, l, a.L, a.m, a.abs_,
                                               a.cbs, slice, lane);
     }
-    publish(ver + l, (int)(k + 1), lane);
+    }
+    publish_levels(ver, l0, 2, n, (int)(k + 1), lane);
     q = __shfl_sync(0xffffffffu, q0, 0);
   }
 }
@@ -170,11 +181,13 @@ struct LpFused {
   unsigned long long* claim;
   Header* hdr;
   unsigned long long wait_ns;
+  int lpu;             // levels per unit (1, 2, 4)
+  int bps;             // resident blocks per SM (0: all the kernel's occupancy allows)
 };
 
-// Grid: every block the kernel's occupancy allows on every SM (the correction
-// sweeps are memory-latency bound, so more resident warps help), but no more
-// warps than levels.
+// Grid: bps blocks per SM, by default every block the kernel's occupancy
+// allows (the correction sweeps are memory-latency bound, so more resident
+// warps help), but no more warps than units of one half-sweep.
 template <typename T, int G, int GF, bool C, int SMALL = 0>
 cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int num_sms, cudaStream_t s) {
   const size_t smem = (size_t)kWarpsPerBlock * 3 * LpSlice<T, G, GF>::SL * sizeof(float);
@@ -191,10 +204,12 @@ cudaError_t lp_fused_launch(const LpArgs& a, const LpFused& f, int num_sms, cuda
     if (e != cudaSuccess) return e;
     occ = o < 1 ? 1 : o;
   }
-  int64_t nb = (int64_t)occ * num_sms;
-  const int64_t need = (a.L + kWarpsPerBlock - 1) / kWarpsPerBlock;
+  const int bps = (f.bps > 0 && f.bps < occ) ? f.bps : occ;
+  int64_t nb = (int64_t)bps * num_sms;
+  const int64_t units = (a.L + f.lpu - 1) / f.lpu;
+  const int64_t need = (units + kWarpsPerBlock - 1) / kWarpsPerBlock;
   if (nb > need) nb = need;
-  k_sweeps_lp<T, G, GF, C, SMALL><<<(int)nb, 256, smem, s>>>(a, f.K, f.ver, f.claim, f.hdr,
+  k_sweeps_lp<T, G, GF, C, SMALL><<<(int)nb, 256, smem, s>>>(a, f.K, f.lpu, f.ver, f.claim, f.hdr,
                                                               f.wait_ns);
   return cudaGetLastError();
 }
@@ -240,7 +255,8 @@ cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const
                              float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
                              int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
                              unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
-                             int num_sms, cudaStream_t s) {
+                             int num_sms, int lpu, int bps, cudaStream_t s) {
+  if (lpu != 1 && lpu != 2 && lpu != 4) return cudaErrorInvalidValue;
   const int nb = num_sms;
   LpArgs a{};
   a.A = A;
@@ -254,7 +270,7 @@ cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const
   a.parity = parity;
   a.abs_ = abs_;
   a.cbs = cbs;
-  const LpFused f{K, ver, claim, hdr, wait_ns};
+  const LpFused f{K, ver, claim, hdr, wait_ns, lpu, bps};
   if (bf16 && m <= 128)
     return coupled ? lp_dispatch<Bf16x2, true>(a, f, nb, s) : lp_dispatch<Bf16x2, false>(a, f, nb, s);
   if (bf16)

@@ -203,12 +203,14 @@ cudaError_t launch_check_scale(const double* x0, double* x, int64_t n, Header* h
 cudaError_t launch_lp_convert(const double* src, void* dst, int bf16, float* sc, int sc_stride,
                               const Layout& lay, int64_t dbs, cudaStream_t s);
 // All K correction sweeps of a refinement step in one launch (ver, claim:
-// zeroed counters as for launch_sweeps_fused; parity of half-sweep 1).
+// zeroed counters as for launch_sweeps_fused; parity of half-sweep 1); lpu:
+// levels per claimed unit (1, 2 or 4); bps: resident blocks per SM (0: the
+// kernel's occupancy).
 cudaError_t launch_sweeps_lp(const void* A, const void* B, const float* C, const float* sc,
                              float* d, const float* q, int64_t L, int m, int parity, int64_t abs_,
                              int64_t cbs, int bf16, int coupled, int64_t K, int* ver,
                              unsigned long long* claim, Header* hdr, unsigned long long wait_ns,
-                             int num_sms, cudaStream_t s);
+                             int num_sms, int lpu, int bps, cudaStream_t s);
 cudaError_t launch_update(const double* pi, const float* d, double* out, int64_t N, double* bpart,
                           int nb, Header* hdr, double* s_out, cudaStream_t s);
 

@@ -113,8 +113,21 @@ __global__ void __launch_bounds__(kNormThreads) k_normalise(NormArgs a) {
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   const bool vec = ((((uintptr_t)a.x_old) | ((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0;
   if (!a.x_old) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
-      a.x_new[i] = a.z[i] * inv;
+    if (((((uintptr_t)a.x_new) | ((uintptr_t)a.z)) & 15u) == 0) {
+      // 16-byte loads and stores (the destination may be page-locked host
+      // memory, written over the CPU-GPU link)
+      const int64_t n2 = a.N / 2;
+      const double2* z2 = reinterpret_cast<const double2*>(a.z);
+      double2* y2 = reinterpret_cast<double2*>(a.x_new);
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n2; i += stride) {
+        const double2 v = z2[i];
+        y2[i] = make_double2(v.x * inv, v.y * inv);
+      }
+      if (blockIdx.x == 0 && threadIdx.x == 0 && (a.N & 1)) a.x_new[a.N - 1] = a.z[a.N - 1] * inv;
+    } else {
+      for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < a.N; i += stride)
+        a.x_new[i] = a.z[i] * inv;
+    }
   } else if (vec) {
     // batches of kNormV pairs per thread: all loads of a batch are issued
     // before its stores (x_new may alias x_old entry by entry)

@@ -78,3 +78,34 @@ def test_low_precision_needs_m_multiple_of_4():
     blocks = synth.qbd(8, 6, 0.85, seed=1)
     with pytest.raises(ValueError):
         mc.Chain(*(dev(b) for b in blocks), dtype="bf16")
+
+
+@pytest.mark.parametrize("dtype,apply,m", [("bf16", "coupled", 64), ("f32", "inverse", 64),
+                                           ("bf16", "inverse", 128), ("bf16", "coupled", 16),
+                                           ("f64", "inverse", 64)])
+def test_tuning_changes_no_result(dtype, apply, m):
+    """mc_tune picks a launch configuration (blocks per SM, levels per claimed
+    unit) by timing; every configuration gives bitwise the same iterates, and
+    a solve after tuning still matches the oracle."""
+    L = 150
+    blocks = synth.qbd(L, m, 0.8, seed=60 + m, level_dependent=True)
+    ch = mc.Chain(*(torch.from_numpy(b).cuda() for b in blocks), dtype=dtype, apply=apply)
+    N = L * m
+    x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    ref, _ = ch.solve(tol=0.0, maxit=96, check_every=32)
+    bps, lpu, ms = ch.tune(x, 32)
+    assert ms > 0 and bps >= 0 and lpu in (1, 2, 4)
+    assert ch.tuning() == (bps, lpu)
+    cands = [(0, 1), (2, 2), (3, 4)] if dtype != "f64" else [(0, 1), (1, 1), (2, 1)]
+    for b, u in cands:
+        ch.set_tuning(b, u)
+        out, _ = ch.solve(tol=0.0, maxit=96, check_every=32)
+        assert torch.equal(out, ref), (b, u)
+    if dtype == "f64":
+        with pytest.raises(mc.McError):
+            ch.set_tuning(0, 2)          # FP64 sweeps take one level per unit
+    ch.set_tuning(bps, lpu)
+    pi, res = ch.solve(tol=1e-12, maxit=400000, check_every=32)
+    sol = oracle.Chain(*blocks).solve(tol=1e-13, maxit=400000, check_every=32)["x"]
+    assert res["converged"] and np.abs(pi.cpu().numpy() - sol).sum() / np.abs(sol).sum() <= 1e-10
+    ch.close()
