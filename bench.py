@@ -168,6 +168,12 @@ def oracle_sample_rate(name, seconds=15.0, max_levels=4096, threads=0):
                         f"{Ls} of {L} levels (m={m}), {cores} threads, scaled by {Ls}/{L}", k, t
 
 
+def oracle_threads_restore():
+    """Back to every host core for the oracle (after a single-thread sample)."""
+    import oracle
+    oracle.threads(os.cpu_count() or 1)
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -398,6 +404,10 @@ def run_mine(args):
     if ws == 1 and not args.no_cpu_baseline:
         rate, cores, sample, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
+        # the same oracle on one host thread (a shorter sample of the same levels)
+        r1, c1, s1, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds / 3, threads=1)
+        cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": c1, "sample": s1}
+        oracle_threads_restore()
     if args.dtype == "f64":
         kname = ("k_sweeps_banded" if banded else "k_sweeps") if fused else "k_phase"
         key = f"{name}:{args.apply}"
