@@ -422,7 +422,8 @@ def run_mine(args):
         # counters taken on an older kernel source do not describe this one
         if tk and key in tk["workloads"] and tk["kernel_src_sha256"] == src_hash(tk["sources"]):
             w = tk["workloads"][key]
-            traffic = w["bytes_per_sweep"] * sweeps_per_launch if fused else w["bytes_per_launch"]
+            traffic = (w["bytes_per_sweep"] * sweeps_per_launch + w.get("tail_bytes", 0)
+                       if fused else w["bytes_per_launch"])
     if args.dtype == "f64":
         roof = {"bound": "alu", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
