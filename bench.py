@@ -649,11 +649,20 @@ def run_contraction(args):
     N = L * m
     rows = {}
     w = min(args.refine_every, 1024)
+    # --warm-start S: every splitting starts from the type-1 stair iterate after
+    # S sweeps from uniform, so that all are timed over the same late window
+    x_start = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    if args.warm_start > 0:
+        ch = mcl.Chain(*d, stair=1)
+        x_start, _ = ch.solve(tol=0.0, eps=0.0, maxit=args.warm_start,
+                              check_every=min(w, args.warm_start), raise_on_maxit=False)
+        torch.cuda.synchronize()
+        ch.close()
     for stair, label, nsw in ((1, "stair1", args.steps), (2, "stair2", args.steps),
                               (4, "block_gauss_seidel", args.steps),
                               (3, "block_jacobi", args.bj_steps)):
         ch = mcl.Chain(*d, stair=stair)
-        x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+        x = x_start.clone()
         pi = torch.empty_like(x)
         torch.cuda.synchronize()
         traj, done, t = [], 0, 0.0
@@ -672,7 +681,8 @@ def run_contraction(args):
                        "trajectory": traj}
         ch.close()
     print(json.dumps({"mode": "contraction", "workload": name, "L": L, "m": m,
-                      "window": w, "segment": args.segment, "results": rows}), flush=True)
+                      "window": w, "segment": args.segment, "warm_start": args.warm_start,
+                      "results": rows}), flush=True)
 
 
 def measure_fp64_peak():
@@ -763,6 +773,9 @@ def main():
     ap.add_argument("--contraction", action="store_true",
                     help="contraction factors of stair / block Jacobi / block Gauss-Seidel")
     ap.add_argument("--bj-steps", type=int, default=20000)
+    ap.add_argument("--warm-start", type=int, default=0,
+                    help="contraction mode: start every splitting from the type-1 stair iterate "
+                         "after this many sweeps from uniform")
     ap.add_argument("--segment", type=int, default=16384,
                     help="contraction mode: sweeps between recorded contraction factors")
     ap.add_argument("--requests", type=int, default=16)
