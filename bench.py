@@ -140,19 +140,22 @@ def aggregate(ms, e2e_s, steps, e2e_steps, ws, device="cpu"):
     return ms, e2e_s, ws * steps / (ms * 1e-3), ws * e2e_steps / e2e_s
 
 
-def oracle_sample_rate(name, seconds=15.0, max_levels=4096, threads=0):
-    """CPU oracle sweeps/s on a bounded sample (the first levels of the same
-    workload), scaled to the full workload's sweeps/s by the level ratio."""
+def oracle_sample_rate(name, seconds=15.0, max_levels=None, threads=0, oc=None):
+    """CPU oracle sweeps/s on the workload (whole by default; the first
+    max_levels levels scaled by the level ratio otherwise), timed for about
+    `seconds` after one untimed sweep.  oc: an oracle chain of the workload
+    already built (reused between calls)."""
     import numpy as np
 
     import oracle
     import synth
 
     L, m = synth.workload_shape(name)
-    Ls = min(L, max_levels)
-    blocks = synth.workload(name, 0, Ls)
-    oc = oracle.Chain(*blocks)
-    del blocks
+    Ls = L if max_levels is None else min(L, max_levels)
+    if oc is None:
+        blocks = synth.workload(name, 0, Ls)
+        oc = oracle.Chain(*blocks)
+        del blocks
     cores = oracle.threads(threads)
     N = Ls * m
     x = np.full(N, 1.0 / N)
@@ -164,8 +167,9 @@ def oracle_sample_rate(name, seconds=15.0, max_levels=4096, threads=0):
     oc.sweeps(x, k)
     t = time.perf_counter() - t0
     rate = k / t * (Ls / L)
-    return rate, cores, f"{k} oracle sweeps (Algorithm 2 + Eq. (2) normalisation) of the first " \
-                        f"{Ls} of {L} levels (m={m}), {cores} threads, scaled by {Ls}/{L}", k, t
+    what = (f"all {L} levels" if Ls == L else f"the first {Ls} of {L} levels, scaled by {Ls}/{L}")
+    return rate, cores, f"{k} oracle sweeps (Algorithm 2 + Eq. (2) normalisation) of {what} " \
+                        f"(m={m}), {cores} threads", k, t, oc
 
 
 def oracle_threads_restore():
@@ -185,8 +189,10 @@ def run_reference(args):
 
     name = args.workload
     L, m = synth.workload_shape(name)
-    # size one step (one oracle sweep of a level sample) to ~20 ms of CPU work
-    Ls = min(L, 4096)
+    # one step = one oracle sweep of the whole chain (about 30 ms on 16 cores
+    # for 32768 levels of 64); chains too large for a few-minute run are
+    # sampled by their first levels, scaled by the level ratio
+    Ls = L if L * m * m <= 32768 * 256 * 256 else 4096
     blocks = synth.workload(name, 0, Ls)
     oc = oracle.Chain(*blocks)
     del blocks
@@ -200,8 +206,9 @@ def run_reference(args):
         x = oc.sweeps(x, 1)
     t = time.perf_counter() - t0
     value = args.steps / t * (Ls / L)
-    sample = (f"each step = 1 oracle sweep of the first {Ls} of {L} levels (m={m}), "
-              f"{cores} threads; sweeps/s scaled by {Ls}/{L}")
+    what = (f"all {L} levels" if Ls == L else f"the first {Ls} of {L} levels, sweeps/s scaled "
+            f"by {Ls}/{L}")
+    sample = f"each step = 1 oracle sweep of {what} (m={m}), {cores} threads"
     out = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
            "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * t / args.steps / (Ls / L), "higher_is_better": True,
@@ -402,11 +409,13 @@ def run_mine(args):
         return
     cpu = None
     if ws == 1 and not args.no_cpu_baseline:
-        rate, cores, sample, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds)
+        rate, cores, sample, _, _, oc = oracle_sample_rate(name, seconds=args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample}
-        # the same oracle on one host thread (a shorter sample of the same levels)
-        r1, c1, s1, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds / 3, threads=1)
+        # the same oracle on one host thread (a shorter run on the same chain)
+        r1, c1, s1, _, _, _ = oracle_sample_rate(name, seconds=args.cpu_seconds / 3, threads=1,
+                                                 oc=oc)
         cpu["single_thread"] = {"value": r1, "unit": UNIT, "cores": c1, "sample": s1}
+        del oc
         oracle_threads_restore()
     if args.dtype == "f64":
         kname = ("k_sweeps_banded" if banded else "k_sweeps") if fused else "k_phase"

@@ -15,10 +15,17 @@ What it computes (arXiv 2302.07551):
   * Sect. 3: the stopping rule (step error <= eps or k >= maxit), plus the
     residual ||Q^T pi||_1 <= tol test used by the GPU solver.
 
+Also the mixed-precision refinement step as the library defines it (not in
+the paper): the operators quantized as stored (FP32, or BF16 with a
+power-of-two scale per block: ``quantize_block``, ``round_bf16``), the
+correction sweeps of Algorithm 2 in FP64 (``Chain.refinement_step``).
+
 Pins (tests/test_oracle_*.py, CPU only): Example 1 and Example 2 spectra,
 dense direct solves, the birth-death closed form, invariants, LU
 reconstruction, equal STAIR/BGS spectra on block-tridiagonal matrices and
-Young's relation with block Jacobi, observed contraction vs the eigenvalue.
+Young's relation with block Jacobi, observed contraction vs the eigenvalue;
+BF16 rounding against hand-checked ties and torch's conversion, the FP64
+refinement step against the dense correction sweeps.
 """
 import ctypes
 import os
@@ -181,6 +188,47 @@ class Chain:
         return dict(x=x, sweeps=int(k), resid=float(out[0]), step=float(out[1]),
                     hist=hist[:k] if history else None)
 
+    def refinement_step(self, pi0, K, dtype="f64", apply="inverse", method=STAIR1):
+        """One outer step of the mixed-precision refinement around Eq. (2), with
+        the operators quantized as the library stores them and the arithmetic in
+        FP64: r = Q^T pi0, q = (-T_dd)^{-1} r rounded to FP32 (dtype f32 / bf16);
+        K correction sweeps from d = 0 of Algorithm 2 on Q^T d = -r, each
+        diagonal-only row (then each coupled row, with the fresh neighbours)
+        d_l = C_l (A_l d_{l-1} + B_l d_{l+1}) + q_l (inverse mode: A = T_lo,
+        B = T_up, C = (-T_dd)^{-1} in FP32) or d_l = A_l d_{l-1} + B_l d_{l+1} + q_l
+        (coupled mode: A, B = (-T_dd)^{-1} T_lo, (-T_dd)^{-1} T_up; C unused);
+        then pi = (pi0 + d) / e^T (pi0 + d).  dtype f64 leaves every operator
+        in FP64 (the FP64 correction step)."""
+        L, m = self.L, self.m
+        pi0 = _c64(pi0).reshape(-1)
+        r = self.residual_vec(pi0).reshape(L, m)
+        ninv = np.array([-np.linalg.solve(self.Tdd[l], np.eye(m)) for l in range(L)])
+        q = np.einsum("lij,lj->li", ninv, r)
+        lowp = dtype != "f64"
+        if lowp:
+            q = q.astype(np.float32).astype(np.float64)
+        if apply == "coupled":
+            A = [quantize_block(ninv[l] @ self.Tlo[l], dtype) for l in range(L)]
+            B = [quantize_block(ninv[l] @ self.Tup[l], dtype) for l in range(L)]
+            C = None
+        else:
+            A = [quantize_block(self.Tlo[l], dtype) for l in range(L)]
+            B = [quantize_block(self.Tup[l], dtype) for l in range(L)]
+            C = [quantize_block(ninv[l], "f32" if lowp else "f64") for l in range(L)]
+        first = 0 if method == STAIR1 else 1          # parity of the diagonal-only rows
+        d = np.zeros((L, m))
+        for _ in range(K):
+            for parity in (first, 1 - first):
+                for l in range(parity, L, 2):
+                    g = np.zeros(m)
+                    if l > 0:
+                        g += A[l] @ d[l - 1]
+                    if l < L - 1:
+                        g += B[l] @ d[l + 1]
+                    d[l] = (g if C is None else C[l] @ g) + q[l]
+        x = pi0 + d.reshape(-1)
+        return x / np.sum(x)
+
     def iteration_matrix(self, method=STAIR1):
         """Dense M^{-1} N, column k = unnormalised sweep of e_k (small N only)."""
         assert self.N <= 4096
@@ -203,6 +251,31 @@ class Chain:
             if l < L - 1:
                 T[l * m:(l + 1) * m, (l + 1) * m:(l + 2) * m] = self.Tup[l]
         return T
+
+
+def round_bf16(x):
+    """FP64 values rounded once to BF16 (8 significant bits, round to nearest,
+    ties to even; zeros stay zero), returned as FP64."""
+    x = np.asarray(x, np.float64)
+    mant, ex = np.frexp(x)                     # x = mant 2^ex, 0.5 <= |mant| < 1
+    return np.ldexp(np.rint(np.ldexp(mant, 8)), ex - 8)
+
+
+def quantize_block(B, dtype):
+    """A block as the mixed-precision path stores it: FP32 (round to nearest),
+    or BF16 with one power-of-two scale 2^e per block, e from the block's
+    largest magnitude (max |B| = f 2^e, 0.5 <= f < 1), i.e. 2^e round_bf16(B / 2^e).
+    Returns the FP64 value the stored block represents."""
+    B = np.asarray(B, np.float64)
+    if dtype == "f32":
+        return B.astype(np.float32).astype(np.float64)
+    if dtype == "bf16":
+        mx = np.abs(B).max()
+        e = int(np.frexp(mx)[1]) if mx > 0 else 0
+        return np.ldexp(round_bf16(np.ldexp(B, -e)), e)
+    if dtype == "f64":
+        return B.copy()
+    raise ValueError(dtype)
 
 
 def _seqsum(v):

@@ -444,3 +444,59 @@ def test_block_hessenberg_stair_rate_close_to_gauss_seidel():
     g_bs, g_bgs = gamma(oracle.STAIR1), gamma(oracle.BGS)
     rho2 = np.log(1 / g_bgs) / np.log(1 / g_bs)
     assert 0.5 < rho2 < 2.0
+
+
+# --- mixed-precision storage and the refinement step --------------------------------
+
+def test_round_bf16_ties_and_torch():
+    """BF16 keeps 8 significant bits, rounding to nearest with ties to even."""
+    r = oracle.round_bf16
+    one = 1.0
+    assert r(one + 2.0 ** -8) == 1.0                 # tie, 1.0 is even
+    assert r(one + 3 * 2.0 ** -8) == 1.0 + 2.0 ** -6  # tie, rounds to the even neighbour
+    assert r(one + 2.0 ** -8 + 2.0 ** -20) == 1.0 + 2.0 ** -7
+    assert r(-(one + 3 * 2.0 ** -8)) == -(1.0 + 2.0 ** -6)
+    assert r(0.0) == 0.0 and r(0.75) == 0.75
+    torch = pytest.importorskip("torch")
+    x = np.random.default_rng(4).standard_normal(20000).astype(np.float32).astype(np.float64)
+    ref = torch.from_numpy(x.astype(np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(r(x), ref)
+
+
+def test_quantize_block_scale_and_grid():
+    rng = np.random.default_rng(9)
+    B = rng.random((16, 16)) * 37.0
+    Q = oracle.quantize_block(B, "bf16")
+    e = int(np.frexp(np.abs(B).max())[1])
+    S = Q / 2.0 ** e
+    assert 0.5 <= np.abs(S).max() <= 1.0                        # scale from the block max
+    assert np.array_equal(oracle.round_bf16(S), S)              # mantissas on the BF16 grid
+    assert np.abs(Q - B).max() <= 2.0 ** -9 * 2.0 ** e          # half a BF16 ulp at the top
+    assert np.array_equal(oracle.quantize_block(B, "f32"), B.astype(np.float32).astype(np.float64))
+    assert np.array_equal(oracle.quantize_block(np.zeros((3, 3)), "bf16"), np.zeros((3, 3)))
+
+
+@pytest.mark.parametrize("apply", ["inverse", "coupled"])
+@pytest.mark.parametrize("method", [oracle.STAIR1, oracle.STAIR2])
+def test_refinement_step_fp64_equals_correction_sweeps(apply, method):
+    """Without quantization the refinement step is K correction sweeps
+    z = M^{-1}(N z - r) from zero (the pinned or_sweep_rhs), then the
+    renormalised pi0 + z; the explicit inverse and the coupled operators give
+    the LU solves' values up to rounding."""
+    L, m, K = 9, 6, 7
+    dn, loc, up = synth.qbd(L, m, 0.85, seed=70, level_dependent=True)
+    ch = oracle.Chain(dn, loc, up)
+    pi0 = np.random.default_rng(2).random(L * m)
+    pi0 /= pi0.sum()
+    r = ch.residual_vec(pi0)
+    d = np.zeros(L * m)
+    for _ in range(K):
+        d = ch.sweep_rhs(d, -r, method)
+    ref = (pi0 + d) / (pi0 + d).sum()
+    got = ch.refinement_step(pi0, K, "f64", apply, method)
+    assert np.abs(got - ref).sum() <= 1e-13 * np.abs(ref).sum()
+    # low-precision storage moves the step by its rounding only
+    for dtype, tol in (("f32", 1e-6), ("bf16", 2e-2)):
+        q = ch.refinement_step(pi0, K, dtype, apply, method)
+        err = np.abs(q - ref).sum() / np.abs(ref).sum()
+        assert 0.0 < err <= tol, (dtype, err)
