@@ -78,6 +78,12 @@ def test_create_rejects_bad_arguments_before_any_gpu_work(lib):
         assert getattr(lib, f)(None) == nat.MC_ERR_ARG
     assert lib.mc_sweep(None, fake, fake, 1, None) == nat.MC_ERR_ARG
     assert lib.mc_solve(None, None, fake, 1e-12, 0.0, 10, 1, None) == nat.MC_ERR_ARG
+    t = nat.McTuning(0, 1)
+    assert lib.mc_set_tuning(None, ctypes.byref(t)) == nat.MC_ERR_ARG
+    assert lib.mc_get_tuning(None, ctypes.byref(t)) == nat.MC_ERR_ARG
+    assert lib.mc_tune(None, fake, 16, ctypes.byref(t), None) == nat.MC_ERR_ARG
+    n = ctypes.c_int32()
+    assert lib.mc_server_trials(None, None, 0, ctypes.byref(n)) == nat.MC_ERR_ARG
     lib.mc_destroy(None)
 
 
