@@ -694,6 +694,67 @@ def run_contraction(args):
                       "results": rows}), flush=True)
 
 
+def run_host_transfer(args):
+    """Where the end-to-end step's time goes: per call, a one-sweep device call
+    with its sync, the host-buffer call (x read in place from pinned memory by
+    the kernels, pi stored into pinned memory by the normalisation), the same
+    step through the copy engine (16 MB H2D, device sweep, 16 MB D2H), the
+    device sweep followed by the D2H copy, and each 16 MB copy alone."""
+    import torch
+
+    import synth
+    import paper_2302_07551_gb300 as mcl
+
+    torch.cuda.set_device(0)
+    blocks = synth.workload(args.workload)
+    d = [torch.from_numpy(b).cuda() for b in blocks]
+    del blocks
+    ch = mcl.Chain(*d)
+    del d
+    N = ch.N
+    xd = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+    yd = torch.empty_like(xd)
+    xh = torch.empty(N, dtype=torch.float64).pin_memory()
+    xh.copy_(xd.cpu())
+    yh = torch.empty(N, dtype=torch.float64).pin_memory()
+    s = ch.stream
+    out = {}
+
+    def run(name, f, n=60):
+        for _ in range(5):
+            f()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(n):
+            f()
+        torch.cuda.synchronize()
+        out[name] = 1e3 * (time.perf_counter() - t0) / n
+
+    def on(fn):
+        def g():
+            with torch.cuda.stream(s):
+                fn()
+            s.synchronize()
+        return g
+
+    run("device_sweep_ms", on(lambda: ch.sweep(xd, yd, 1)))
+    run("host_buffer_sweep_ms", lambda: ch.sweep_host(xh, yh, 1, stats=False))
+    run("copy_engine_h2d_sweep_d2h_ms", on(lambda: (xd.copy_(xh, non_blocking=True),
+                                                   ch.sweep(xd, yd, 1),
+                                                   yh.copy_(yd, non_blocking=True))))
+    run("device_sweep_then_d2h_ms", on(lambda: (ch.sweep(xd, yd, 1),
+                                               yh.copy_(yd, non_blocking=True))))
+    run("h2d_copy_ms", on(lambda: xd.copy_(xh, non_blocking=True)))
+    run("d2h_copy_ms", on(lambda: yh.copy_(yd, non_blocking=True)))
+    mb = 8 * N / 1e6
+    out["bytes_each_way"] = 8 * N
+    out["h2d_gbs"] = mb / out["h2d_copy_ms"]
+    out["d2h_gbs"] = mb / out["d2h_copy_ms"]
+    print(json.dumps({"mode": "host_transfer", "workload": args.workload, "results": out}),
+          flush=True)
+    ch.close()
+
+
 def measure_fp64_peak():
     """FP64 multiply-add peak of this GPU: the probe library's fma loop
     (libmcprobe.so: 8, 16 or 32 independent chains per thread, unrolled 4x,
@@ -799,9 +860,14 @@ def main():
     ap.add_argument("--no-tune", action="store_true",
                     help="keep the default launch configuration (skip mc_tune at set-up)")
     ap.add_argument("--measure-fp64-peak", action="store_true")
+    ap.add_argument("--host-transfer", action="store_true",
+                    help="time the parts of the end-to-end (host-buffer) step")
     args = ap.parse_args()
     if args.measure_fp64_peak:
         measure_fp64_peak()
+        return
+    if args.host_transfer:
+        run_host_transfer(args)
         return
     if args.warmup < 3:
         args.warmup = 3

@@ -30,11 +30,13 @@ __device__ __forceinline__ int ld_relaxed(const int* p) {
   return v;
 }
 
-// Back-off between polls: 128 ns doubling to 2 us, so that many waiting warps
-// do not flood L2 with polls while the units they wait for run.
+// Back-off between polls: 32 ns doubling to 256 ns.  Polls are relaxed loads
+// (cheap), while a long sleep keeps a warp idle after its neighbours are
+// ready: with block-banded dependencies (a unit waits for a whole band of the
+// previous sweep) a 2 us cap left the FP64 pipe idle 16 % of the time.
 __device__ __forceinline__ unsigned backoff(unsigned ns) {
   __nanosleep(ns);
-  return ns < 2048u ? 2u * ns : ns;
+  return ns < 256u ? 2u * ns : ns;
 }
 
 __device__ __forceinline__ void st_release(int* p, int v) {
@@ -58,7 +60,7 @@ __device__ __forceinline__ void wait_neighbours(const int* ver, int64_t l, int64
   const bool lo = l > 0, up = l < L - 1;
   if (lane == 0) {
     unsigned long long t0 = 0;
-    unsigned ns = 128;
+    unsigned ns = 32;
     for (int it = 0;; ++it) {
       const bool ok = (!lo || ld_relaxed(ver + l - 1) >= need) &&
                       (!up || ld_relaxed(ver + l + 1) >= need);
@@ -85,7 +87,7 @@ __device__ __forceinline__ void wait_neighbours2(const int* ver, int64_t l, int6
   const bool lo = l > 0 && need_lo > 0, up = l < L - 1 && need_up > 0;
   if (lane == 0) {
     unsigned long long t0 = 0;
-    unsigned ns = 128;
+    unsigned ns = 32;
     for (int it = 0;; ++it) {
       const bool ok = (!lo || ld_relaxed(ver + l - 1) >= need_lo) &&
                       (!up || ld_relaxed(ver + l + 1) >= need_up);
@@ -152,7 +154,7 @@ __device__ __forceinline__ void wait_band(const int* ver, int64_t l, int64_t L, 
   bool ok = !mine || ld_relaxed(ver + j) >= nj;
   if (!__all_sync(0xffffffffu, ok)) {
     const unsigned long long t0 = global_ns();
-    unsigned ns = 128;
+    unsigned ns = 32;
     while (true) {
       ns = backoff(ns);
       if (!ok) ok = ld_relaxed(ver + j) >= nj;
@@ -179,7 +181,7 @@ __device__ __forceinline__ void wait_levels(const int* ver, int64_t first, int s
   bool ok = !mine || ld_relaxed(ver + j) >= need;
   if (!__all_sync(0xffffffffu, ok)) {
     const unsigned long long t0 = global_ns();
-    unsigned ns = 128;
+    unsigned ns = 32;
     while (true) {
       ns = backoff(ns);
       if (!ok) ok = ld_relaxed(ver + j) >= need;
