@@ -438,7 +438,7 @@ def run_mine(args):
                 "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS,
                 "traffic": traffic,
                 "kernel": f"{kname} (fused: {sweeps_per_launch} sweeps + residual units per launch)",
-                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz (the pipe rate implied by ncu's FP64-pipe utilisation of this kernel)",
+                "peak_source": "derived: 152 SMs x 2 FP64 lanes/clk x 2 flop x 2.07 GHz; the fma-loop probe (--measure-fp64-peak) measures 1.2558 TFLOP/s = 1.996 lanes/clk/SM",
                 "hbm": {"achieved": achieved_gbs, "peak": hbm_peak, "unit": "GB/s",
                         "frac": achieved_gbs / hbm_peak, "peak_source": hbm_src}}
     else:
