@@ -100,21 +100,23 @@ __global__ void __launch_bounds__(256) k_b_sweeps(const BTable* __restrict__ t, 
     if (u.h2 || u.k > 0)
       wait_levels(Q->ver, u.l - 1, 2, u.n + 1, Q->L, base + (int)(u.h2 ? u.k + 1 : u.k),
                   &out[u.r].status, lane, kWaitNs);
+    const bool want = u.k >= K - 2;   // e^T z of the last two sweeps only
     for (int i = 0; i < u.n; ++i) {
       const int64_t l = u.l + 2 * i;
       double ls;
       if constexpr (RMAX == 8) {
         ls = level_sweep2<8, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l,
-                                                         Q->L, Q->m, Q->ms, slice, lane);
+                                                         Q->L, Q->m, Q->ms, slice, lane, 1.0,
+                                                         nullptr, nullptr, nullptr, want);
       } else {
         switch (Q->R) {
-          case 1: ls = level_sweep2<1, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane); break;
-          case 2: ls = level_sweep2<2, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane); break;
-          case 3: ls = level_sweep2<RMAX == 4 ? 3 : 2, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane); break;
-          default: ls = level_sweep2<RMAX, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane); break;
+          case 1: ls = level_sweep2<1, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane, 1.0, nullptr, nullptr, nullptr, want); break;
+          case 2: ls = level_sweep2<2, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane, 1.0, nullptr, nullptr, nullptr, want); break;
+          case 3: ls = level_sweep2<RMAX == 4 ? 3 : 2, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane, 1.0, nullptr, nullptr, nullptr, want); break;
+          default: ls = level_sweep2<RMAX, COUPLED, false, true, true>(Q->A, Q->B, Q->C, src, src, dst, l, Q->L, Q->m, Q->ms, slice, lane, 1.0, nullptr, nullptr, nullptr, want); break;
         }
       }
-      if (lane == 0) Q->lsum2[(u.k & 1) * Q->L + l] = ls;
+      if (want && lane == 0) Q->lsum2[(u.k & 1) * Q->L + l] = ls;
     }
     publish_levels(Q->ver, u.l, 2, u.n, base + (int)u.k + 1, lane);
     q = __shfl_sync(kFull, q0, 0);

@@ -78,9 +78,12 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps(FusedArgs a) {
     const double* src = h2 ? dst : (k == 0 ? a.x_in : a.W);
     const int need = (int)(h2 ? k + 1 : k);
     if (need > 0) wait_neighbours(a.ver, l, a.L, need, &a.hdr->status, lane, a.wait_ns);
+    // e^T z is needed of the last two sweeps only
+    const bool want = k >= a.K - 2;
     const double t = level_sweep2<R, COUPLED, PAIRED, true, true>(
-        a.A, a.B, a.C, src, src, dst, l, a.L, a.m, a.ms, slice, lane);
-    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+        a.A, a.B, a.C, src, src, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, nullptr, nullptr,
+        nullptr, want);
+    if (want && lane == 0) a.lsum[(k & 1) * a.L + l] = t;
     publish(a.ver + l, (int)(k + 1), lane);
     q = __shfl_sync(kFull, q0, 0);
   }
@@ -115,9 +118,10 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs 
       wait_band(a.ver, l, a.L, a.bw, (int)k, (int)(h2 ? k + 1 : k), &a.hdr->status, lane,
                 a.wait_ns);
     const double* near = h2 ? dst : y;
+    const bool want = k >= a.K - 2;
     const double t = level_sweep2<R, false, false, true, true>(
-        a.A, a.B, a.C, near, near, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, a.far, y, y);
-    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+        a.A, a.B, a.C, near, near, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, a.far, y, y, want);
+    if (want && lane == 0) a.lsum[(k & 1) * a.L + l] = t;
     publish(a.ver + l, (int)(k + 1), lane);
     q = __shfl_sync(kFull, q0, 0);
   }
@@ -147,9 +151,11 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_bgs_fused(FusedArgs a) {
     double* dst = k == a.K - 1 ? a.Z : a.W;
     const double* up = k == 0 ? a.x_in : a.W;    // z^k at l + 1
     wait_neighbours2(a.ver, l, a.L, (int)(k + 1), (int)k, &a.hdr->status, lane, a.wait_ns);
-    const double t = level_sweep2<R, COUPLED, false, true, true>(a.A, a.B, a.C, dst, up, dst, l,
-                                                                 a.L, a.m, a.ms, slice, lane);
-    if (lane == 0) a.lsum[(k & 1) * a.L + l] = t;
+    const bool want = k >= a.K - 2;
+    const double t = level_sweep2<R, COUPLED, false, true, true>(
+        a.A, a.B, a.C, dst, up, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, nullptr, nullptr,
+        nullptr, want);
+    if (want && lane == 0) a.lsum[(k & 1) * a.L + l] = t;
     publish(a.ver + l, (int)(k + 1), lane);
     q = __shfl_sync(kFull, q0, 0);
   }

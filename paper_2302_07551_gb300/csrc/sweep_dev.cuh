@@ -197,7 +197,10 @@ __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const F
 }
 
 // Returns sum_i z_l[i]: on every lane (WARP_TOTAL) or the lane's own rows
-// only (callers that only need a total over many levels reduce once at the end).
+// only (callers that only need a total over many levels reduce once at the end);
+// want_sum = false skips the sum (0 is returned): the FP64 adds it costs are a
+// share of an FP64-bound kernel, and a fused launch only needs the sums of its
+// last two sweeps.
 // CG: neighbour vectors written by other SMs during this kernel (L2 reads).
 template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true, bool CG = false>
 __device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
@@ -206,7 +209,8 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
                                                double* slice, int lane, double scale = 1.0,
                                                const FarDesc* far = nullptr,
                                                const double* xfar_lo = nullptr,
-                                               const double* xfar_up = nullptr) {
+                                               const double* xfar_up = nullptr,
+                                               bool want_sum = true) {
   constexpr int NA = Tune<R>::NA, W = 32 * R;
   double* v_lo = slice;
   double* v_up = slice + W;
@@ -233,18 +237,26 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
     gemv_acc<R>(acc, C + (size_t)l * ms, v_g, m, lane);
   }
   double ls = 0.0;
+  if (want_sum) {
 #pragma unroll
-  for (int r = 0; r < R; ++r) {
-    const int row = lane + 32 * r;
-    const double zr = fold<R>(acc[r]);
-    if (row < m) {
-      dst[l * m + row] = zr;
-      ls += zr;
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      const double zr = fold<R>(acc[r]);
+      if (row < m) {
+        dst[l * m + row] = zr;
+        ls += zr;
+      }
+    }
+    if (WARP_TOTAL) ls = warp_sum(ls);
+  } else {
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int row = lane + 32 * r;
+      if (row < m) dst[l * m + row] = fold<R>(acc[r]);
     }
   }
-  const double total = WARP_TOTAL ? warp_sum(ls) : ls;
   __syncwarp();   // the slice is rewritten for the next level
-  return total;
+  return ls;
 }
 
 // Residual of a sweep's result at a diagonal-only stair row l, from the
