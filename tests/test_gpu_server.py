@@ -44,12 +44,14 @@ def test_server_results_match_oracle(dtype):
     srv.close()
 
 
+@pytest.mark.parametrize("autotune", [False, True])
 @pytest.mark.parametrize("dtype", ["f64", "bf16"])
-def test_server_coupled_stair2_matches_oracle(dtype):
+def test_server_coupled_stair2_matches_oracle(dtype, autotune):
     """The server in coupled mode with the type-2 stair matrix: each request's
-    pi against the oracle's solution (STAIR2 solve of the same chain)."""
+    pi against the oracle's solution (STAIR2 solve of the same chain); tuned,
+    the units group levels of the type-2 half-sweeps (the other parity)."""
     srv = mc.Server(2 << 30, dtype=dtype, apply="coupled", stair=2, tol=1e-12, check_every=32,
-                    autotune=False)
+                    autotune=autotune)
     mix = [(40, 16, 0.6), (64, 64, 0.7), (33, 128, 0.9), (9, 200, 0.85)]
     for i, (L, m, ratio) in enumerate(mix):
         assert srv.submit(i, *blocks_for(i, L, m, ratio))
