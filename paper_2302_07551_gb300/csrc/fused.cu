@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs 
 // last sweep writes Z): a unit overwrites z^k_l only after its two readers,
 // (k, l-1) and (k-1, l+1), have completed, which is what it waits for.
 template <int R, bool COUPLED>
-__global__ void __launch_bounds__(256, Tune<R>::MINB) k_bgs_fused(FusedArgs a) {
+__global__ void __launch_bounds__(256, 2) k_bgs_fused(FusedArgs a) {
   extern __shared__ double vsh[];
   const int lane = threadIdx.x & 31;
   double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
@@ -152,7 +152,9 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_bgs_fused(FusedArgs a) {
     const double* up = k == 0 ? a.x_in : a.W;    // z^k at l + 1
     wait_neighbours2(a.ver, l, a.L, (int)(k + 1), (int)k, &a.hdr->status, lane, a.wait_ns);
     const bool want = k >= a.K - 2;
-    const double t = level_sweep2<R, COUPLED, false, true, true>(
+    // few warps run (one per sweep in flight), each on the critical path:
+    // twice the columns per load batch, so a unit streams in half the round trips
+    const double t = level_sweep2<R, COUPLED, false, true, true, R <= 4 ? 2 : 1>(
         a.A, a.B, a.C, dst, up, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, nullptr, nullptr,
         nullptr, want);
     if (want && lane == 0) a.lsum[(k & 1) * a.L + l] = t;

@@ -41,12 +41,13 @@ struct Tune {
 
 // acc[r][c] += M(row_r, j) * v[j] for the m columns j of a column-major block
 // M; column j feeds accumulator j % NA.  v: per-warp shared slice, zero
-// beyond m (so the pair load at an odd m reads a zero).
-template <int R>
+// beyond m (so the pair load at an odd m reads a zero).  UM multiplies the
+// columns per batch (more loads in flight for kernels with few warps).
+template <int R, int UM = 1>
 __device__ __forceinline__ void gemv_acc(double (&acc)[R][Tune<R>::NA],
                                          const double* __restrict__ M, const double* v, int m,
                                          int lane) {
-  constexpr int U = Tune<R>::U, NA = Tune<R>::NA;
+  constexpr int U = Tune<R>::U * UM, NA = Tune<R>::NA;
   for (int j0 = 0; j0 < m; j0 += U) {
     double t[U][R];
 #pragma unroll
@@ -202,7 +203,8 @@ __device__ __forceinline__ void far_terms(double (&acc)[R][Tune<R>::NA], const F
 // share of an FP64-bound kernel, and a fused launch only needs the sums of its
 // last two sweeps.
 // CG: neighbour vectors written by other SMs during this kernel (L2 reads).
-template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true, bool CG = false>
+template <int R, bool COUPLED, bool PAIRED = false, bool WARP_TOTAL = true, bool CG = false,
+          int UM = 1>
 __device__ __forceinline__ double level_sweep2(const double* A, const double* B, const double* C,
                                                const double* src, const double* src_up,
                                                double* dst, int64_t l, int64_t L, int m, int ms,
@@ -225,8 +227,8 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
     if (has_lo) gemv_lo_paired<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
     if (has_up) gemv_up_paired<R>(acc, B + (size_t)l * ms, v_up, m, lane);
   } else {
-    if (has_lo) gemv_acc<R>(acc, A + (size_t)l * ms, v_lo, m, lane);
-    if (has_up) gemv_acc<R>(acc, B + (size_t)l * ms, v_up, m, lane);
+    if (has_lo) gemv_acc<R, UM>(acc, A + (size_t)l * ms, v_lo, m, lane);
+    if (has_up) gemv_acc<R, UM>(acc, B + (size_t)l * ms, v_up, m, lane);
   }
   if (far) far_terms<R, CG>(acc, far, xfar_lo, xfar_up, l, L, m, ms, v_lo, lane);
   if (!COUPLED) {
@@ -234,7 +236,7 @@ __device__ __forceinline__ double level_sweep2(const double* A, const double* B,
     for (int r = 0; r < R; ++r) v_g[lane + 32 * r] = fold<R>(acc[r]);
     __syncwarp();
     zero_acc<R>(acc);
-    gemv_acc<R>(acc, C + (size_t)l * ms, v_g, m, lane);
+    gemv_acc<R, UM>(acc, C + (size_t)l * ms, v_g, m, lane);
   }
   double ls = 0.0;
   if (want_sum) {
