@@ -179,7 +179,8 @@ int mc_factor(mc_chain* chain);
  * then x <- z / e^T z and step = ||x_new - x_old||_1.
  *   x_in, x_out: device vectors of N doubles (x_in is not modified unless it
  *     equals x_out; in-place is allowed).  x_in should satisfy e^T x_in = 1
- *     for step to be the paper's step error.
+ *     for step to be the paper's step error.  (desc.stair 3 and 4 run block
+ *     Jacobi and block Gauss-Seidel sweeps with the same interface.)
  *   nsweeps >= 1.
  *   stats_dev: NULL or device array of 3 doubles receiving, for the last
  *     sweep, [e^T z, ||x_new - x_old||_1, ||Q^T x_out||_1].  The residual
@@ -191,13 +192,15 @@ int mc_factor(mc_chain* chain);
  *     at the end of the last fused launch.  Other chains (block-banded,
  *     block Jacobi / Gauss-Seidel) compute the direct residual.  With
  *     stats_dev == NULL no residual is formed.
- * Block-tridiagonal chains with a stair splitting (desc.stair 1 or 2) run the
- * nsweeps sweeps as one persistent launch per 1024 sweeps, with no
- * normalisation between the sweeps of a launch (the scale of the iterate
- * does not change the next one, Eq. (2) up to rounding); x_out is normalised
- * and stats refer to the last sweep as above.  Results are bitwise
- * reproducible for equal calls; a run split into several calls agrees up to
- * rounding.
+ * Stair splittings (desc.stair 1 or 2, block-tridiagonal or banded) and block
+ * Gauss-Seidel on block-tridiagonal chains run the nsweeps sweeps as one
+ * persistent launch per 1024 sweeps, with no normalisation between the sweeps
+ * of a launch (the scale of the iterate does not change the next one, Eq. (2)
+ * up to rounding); x_out is normalised and stats refer to the last sweep as
+ * above.  Block Jacobi (and banded block Gauss-Seidel) run one launch per
+ * sweep.  Results are bitwise reproducible for equal calls and independent of
+ * the launch configuration (mc_set_tuning); a run split into several calls
+ * agrees up to rounding.
  * Async.  Errors: MC_ERR_ARG, MC_ERR_NOT_FACTORED, MC_ERR_CUDA; a breakdown
  * (e^T z <= 0 or not finite) is latched on the device (MC_ERR_BREAKDOWN);
  * MC_ERR_TIMEOUT if a bounded device-side wait of the fused launch gave up
