@@ -750,6 +750,14 @@ def run_host_transfer(args):
     out["bytes_each_way"] = 8 * N
     out["h2d_gbs"] = mb / out["h2d_copy_ms"]
     out["d2h_gbs"] = mb / out["d2h_copy_ms"]
+    # the link's rate on copies long enough that the per-call sync does not count
+    big = 1 << 27
+    bh = torch.empty(big, dtype=torch.float64).pin_memory()
+    bd = torch.empty(big, dtype=torch.float64, device="cuda")
+    run("h2d_copy_1GiB_ms", on(lambda: bd.copy_(bh, non_blocking=True)), n=10)
+    run("d2h_copy_1GiB_ms", on(lambda: bh.copy_(bd, non_blocking=True)), n=10)
+    out["h2d_1GiB_gbs"] = 8 * big / 1e6 / out["h2d_copy_1GiB_ms"]
+    out["d2h_1GiB_gbs"] = 8 * big / 1e6 / out["d2h_copy_1GiB_ms"]
     print(json.dumps({"mode": "host_transfer", "workload": args.workload, "results": out}),
           flush=True)
     ch.close()

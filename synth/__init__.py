@@ -40,6 +40,9 @@ WORKLOADS = {
     # L=4096, m=64, level-dependent, up/down rate ratio 0.8, jump rates halve per level
     "hessenberg_L4096_m64": dict(kind="banded", L=4096, m=64, p=1, q=4, ratio=0.8, decay=0.5,
                                  seed=5),
+    # same recipe at L=32768 (6.4 GB of FP64 blocks): the band waits at the bench's level count
+    "hessenberg_L32768_m64": dict(kind="banded", L=32768, m=64, p=1, q=4, ratio=0.8, decay=0.5,
+                                  seed=5),
     # jumps +-1, +-2 on L=8192 levels of m=128, paired to 4096 levels of 256
     "penta_L8192_m128": dict(kind="penta", L=8192, m=128, ratio=0.8, scale2=0.3, seed=2),
     # same recipe at L=2048 (1024 paired levels of 256; 1.3 GB per sweep): profiling size
