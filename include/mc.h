@@ -383,7 +383,9 @@ int mc_server_step(mc_server* server, int32_t* n_active, int32_t* n_done);
 /*
  * Pop the oldest finished request: tag, pi (host, n_cap >= its N; pi_host may
  * be NULL to discard), result and status (MC_OK, MC_ERR_NO_CONVERGENCE,
- * MC_ERR_SINGULAR_BLOCK, MC_ERR_BREAKDOWN).  MC_ERR_ARG when none is finished.
+ * MC_ERR_SINGULAR_BLOCK, MC_ERR_BREAKDOWN; MC_ERR_CUDA or MC_ERR_ARG when its
+ * pi could not be copied out at retirement, and then pi_host is left as is).
+ * MC_ERR_ARG when none is finished.
  */
 int mc_server_fetch(mc_server* server, int64_t* tag, double* pi_host, int64_t n_cap,
                     mc_result* res, int32_t* status);

@@ -179,6 +179,13 @@ int retire(mc_server* s, size_t i, int status, double resid, double step, double
   dn.res.step_l1 = step;
   dn.res.contraction = kappa;
   dn.res.converged = converged;
+  // a result that could not be copied out is reported as failed, without pi
+  if (rc != MC_OK) {
+    free(dn.pi);
+    dn.pi = nullptr;
+    if (dn.status == MC_OK) dn.status = rc;
+    dn.res.converged = 0;
+  }
   s->done.push_back(dn);
   mc_destroy(r->chain);
   release(s, r->off, r->bytes);

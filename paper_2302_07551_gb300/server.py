@@ -60,7 +60,7 @@ class Server:
         if not self._keep:
             return None
         cap = max(self._keep.values())
-        pi = np.empty(cap)
+        pi = np.full(cap, np.nan)      # stays NaN if the result could not be copied out
         tag = ctypes.c_int64()
         res = nat.McResult()
         st = ctypes.c_int32()
