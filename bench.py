@@ -694,6 +694,67 @@ def run_contraction(args):
                       "results": rows}), flush=True)
 
 
+def run_batch_classes(args):
+    """Batched correction sweeps by block size: for m = 128, 64, 32, 16 the
+    single-chain fused launch (mc_tune's choice) and the solve server's
+    batched launch on requests of that size alone (the autotuner's trials),
+    then on a four-size mix; HBM rate of the sweep launches against the
+    measured copy rate."""
+    import torch
+
+    import synth
+    import paper_2302_07551_gb300 as mcl
+
+    torch.cuda.set_device(0)
+    dtype = args.dtype if args.dtype != "f64" else "bf16"
+    apply = args.apply
+    hbm_peak, hbm_src = peaks()
+    e = 2 if dtype == "bf16" else 4
+
+    def level_bytes(m):
+        return 2 * e * m * m + (0 if apply == "coupled" else 4 * m * m) + 16 * m
+
+    def single(L, m):
+        b = synth.qbd(L, m, 0.9, seed=7, level_dependent=True)
+        ch = mcl.Chain(*(torch.from_numpy(x).cuda() for x in b), dtype=dtype, apply=apply)
+        del b
+        N = L * m
+        x = torch.full((N,), 1.0 / N, dtype=torch.float64, device="cuda")
+        bps, lpu, ms = ch.tune(x, 64)
+        ch.close()
+        gbs = level_bytes(m) * L * 64 / ms / 1e6
+        return dict(L=L, m=m, blocks_per_sm=bps, levels_per_unit=lpu, ms_per_64_sweeps=ms,
+                    gbs=gbs, frac=gbs / hbm_peak)
+
+    def server(mix):
+        srv = mcl.Server(48 << 30, dtype=dtype, apply=apply, tol=1e-30, check_every=64,
+                         maxit=10 ** 9)
+        for i, (L, m) in enumerate(mix):
+            assert srv.submit(i, *synth.qbd(L, m, 0.85, seed=100 + i, level_dependent=True))
+        for _ in range(14):      # the autotuner's trials, then kept-configuration chunks
+            srv.step()
+        tr = srv.trials()
+        srv.close()
+        rows = [dict(blocks_per_sm=t["blocks_per_sm"], levels_per_unit=t["levels_per_unit"],
+                     split64=t["split64"], deep=t["deep"], chosen=t["chosen"],
+                     sweep_ms=t["sweep_ms"], gbs=t["sweep_bytes"] / t["sweep_ms"] / 1e6)
+                for t in tr]
+        best = max(rows, key=lambda r: r["gbs"])
+        return dict(mix=[list(x) for x in mix], best_gbs=best["gbs"],
+                    best_frac=best["gbs"] / hbm_peak, trials=rows)
+
+    out = {"mode": "batch_classes", "dtype": dtype, "apply": apply,
+           "hbm_peak_gbs": hbm_peak, "hbm_peak_source": hbm_src, "single": {}, "batched": {}}
+    for L, m in ((16384, 128), (32768, 64), (32768, 32), (32768, 16)):
+        out["single"]["m%d" % m] = single(L, m)
+    for name, mix in (("m128", [(4096, 128)] * 8), ("m64", [(8192, 64)] * 8),
+                      ("m32", [(8192, 32)] * 16), ("m16", [(8192, 16)] * 16),
+                      ("mix", [(4096, 128)] * 4 + [(8192, 64)] * 4 + [(8192, 32)] * 4
+                       + [(8192, 16)] * 4)):
+        out["batched"][name] = server(mix)
+    print(json.dumps(out), flush=True)
+
+
 def run_host_transfer(args):
     """Where the end-to-end step's time goes: per call, a one-sweep device call
     with its sync, the host-buffer call (x read in place from pinned memory by
@@ -870,12 +931,17 @@ def main():
     ap.add_argument("--measure-fp64-peak", action="store_true")
     ap.add_argument("--host-transfer", action="store_true",
                     help="time the parts of the end-to-end (host-buffer) step")
+    ap.add_argument("--batch-classes", action="store_true",
+                    help="low-precision sweep rate by block size, single chain and batched")
     args = ap.parse_args()
     if args.measure_fp64_peak:
         measure_fp64_peak()
         return
     if args.host_transfer:
         run_host_transfer(args)
+        return
+    if args.batch_classes:
+        run_batch_classes(args)
         return
     if args.warmup < 3:
         args.warmup = 3

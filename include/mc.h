@@ -398,7 +398,8 @@ int mc_server_grid(const mc_server* server, int32_t* blocks, int32_t* threads,
  * One timed chunk of the autotuner (autotune = 1).  For every new batch
  * signature the server times one live chunk per candidate configuration in a
  * coordinate search -- the persistent grid (1, 2, 3, 4, 6, 8 resident
- * 256-thread blocks per SM), then 2 and 4 levels per claimed unit, then the
+ * 256-thread blocks per SM), then 2 and 4 levels per claimed unit (scaled up
+ * for small blocks, see levels_per_unit below), then the
  * other block-size bucketing, then (low precision with blocks of m <= 64)
  * the other load depth -- and keeps the fastest.  The paper trades block
  * size against thread count by hand (Sect. 3); here the trade is measured on
@@ -406,9 +407,10 @@ int mc_server_grid(const mc_server* server, int32_t* blocks, int32_t* threads,
  */
 typedef struct {
   uint64_t signature;       /* bit c set: requests of size class c present (m <= 32, 64,
-                               128, 256); bits 8..: log4 of the total level count     */
+                               128, 256); bits 8..: ceil(log2(total levels)) / 2      */
   int32_t blocks_per_sm;    /* resident 256-thread blocks per SM of the fused launches  */
-  int32_t levels_per_unit;  /* adjacent same-parity levels per claimed unit (1, 2, 4)   */
+  int32_t levels_per_unit;  /* adjacent same-parity levels per claimed unit (1, 2, 4)
+                               for m > 64; x2 for m <= 64, x4 for m <= 32 (at most 16) */
   int32_t split64;          /* 1: blocks of m <= 64 in a launch of their own            */
   int32_t deep;             /* 1: 16 loads in flight per lane for low-precision m <= 64 */
   int32_t chosen;           /* 1: the configuration kept for this signature            */

@@ -40,9 +40,9 @@ __device__ __forceinline__ void class_range(const BTable* t, int c0, int c1, int
 constexpr unsigned long long kWaitNs = 2000000000ull;   // bound of one neighbour wait
 
 // Unit q of a fused chunk of K sweeps over one bucket: sweep k, half-sweep h,
-// request r and its levels l, l + 2, ..., l + 2 (n - 1) (a group of at most G
-// levels of one half-sweep: half-sweep 1 groups [a0, a1) of off_h1, then
-// half-sweep 2 groups [b0, b1) of off_h2).
+// request r and its levels l, l + 2, ..., l + 2 (n - 1) (a group of at most
+// the request's G levels of one half-sweep: half-sweep 1 groups [a0, a1) of
+// off_h1, then half-sweep 2 groups [b0, b1) of off_h2).
 struct BUnit {
   int64_t k, l;
   int r, n;
@@ -50,8 +50,7 @@ struct BUnit {
 };
 
 __device__ __forceinline__ BUnit unit_of(const BTable* t, unsigned long long q, int64_t n1,
-                                         int64_t U, int64_t a0, int64_t b0, int r0, int r1,
-                                         int G) {
+                                         int64_t U, int64_t a0, int64_t b0, int r0, int r1) {
   BUnit u;
   u.k = (int64_t)(q / (unsigned long long)U);
   const int64_t rr = (int64_t)q - u.k * U;
@@ -63,6 +62,7 @@ __device__ __forceinline__ BUnit unit_of(const BTable* t, unsigned long long q, 
   const int par = u.h2 ? 1 - Q->p1 : Q->p1;
   const int64_t P = (Q->L - par + 1) / 2;        // levels of this half-sweep
   const int64_t g = i - off[u.r];
+  const int G = Q->G;
   u.l = 2 * G * g + par;
   const int64_t left = P - (int64_t)G * g;
   u.n = left < G ? (int)left : G;
@@ -85,14 +85,13 @@ __global__ void __launch_bounds__(256) k_b_sweeps(const BTable* __restrict__ t, 
   const int64_t b0 = t->off_h2[r0], b1 = t->off_h2[r1];
   const int64_t n1 = a1 - a0, U = n1 + (b1 - b0);
   if (U == 0) return;
-  const int G = t->G;
   const unsigned long long total = (unsigned long long)K * (unsigned long long)U;
   const int base = t->epoch;
   unsigned long long q0 = claim_unit(claim, lane);
   unsigned long long q = __shfl_sync(kFull, q0, 0);
   while (q < total) {
     q0 = claim_unit(claim, lane);
-    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1, G);
+    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1);
     const BReq* Q = &t->r[u.r];
     const bool last = u.k == K - 1;
     double* dst = last ? Q->z : Q->xb;
@@ -290,14 +289,13 @@ __global__ void __launch_bounds__(256) k_b_sweeps_lp(const BTable* __restrict__ 
   const int64_t b0 = t->off_h2[r0], b1 = t->off_h2[r1];
   const int64_t n1 = a1 - a0, U = n1 + (b1 - b0);
   if (U == 0) return;
-  const int G = t->G;
   const unsigned long long total = (unsigned long long)K * (unsigned long long)U;
   const int base = t->epoch;
   unsigned long long q0 = claim_unit(claim, lane);
   unsigned long long q = __shfl_sync(kFull, q0, 0);
   while (q < total) {
     q0 = claim_unit(claim, lane);
-    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1, G);
+    const BUnit u = unit_of(t, q, n1, U, a0, b0, r0, r1);
     const BReq* Q = &t->r[u.r];
     if (u.h2 || u.k > 0)
       wait_levels(Q->ver, u.l - 1, 2, u.n + 1, Q->L, base + (int)(u.h2 ? u.k + 1 : u.k),

@@ -19,8 +19,9 @@
 // persistent launch per bucket for all sweeps of the chunk, units claimed in
 // order, each waiting for its neighbour levels through the request's
 // completion counters.  A unit covers G adjacent levels of one half-sweep of
-// one request (levels l0, l0 + 2, ..., l0 + 2 (G - 1)): one claim, one wait
-// for the G + 1 neighbour levels, one completion fence.  Counters grow across
+// one request (levels l0, l0 + 2, ..., l0 + 2 (G - 1); G per request, from
+// the table's G and the request's size class): one claim, one wait for the
+// G + 1 neighbour levels, one completion fence.  Counters grow across
 // chunks: a chunk with epoch E writes E + k + 1 after its sweep k, so counters
 // never need resetting (new requests start at zero <= E); the claim counters
 // live in the table and are reset by the table copy that starts every chunk.
@@ -53,18 +54,28 @@ struct BReq {
   int* ver;             // fused sweeps: per-level completion counters
   int64_t L;
   int32_t m, ms, R, p1;  // p1: 0-based parity of the diagonal-only rows
+  int32_t G, pad;        // levels per unit of this request (the table's G scaled by size class)
   int64_t lp_bs, lp_cbs;
 };
 
 // Size classes of the request table: m <= 32, 64, 128, 256.
 constexpr int kClasses = 4;
 __host__ __device__ inline int size_class(int m) { return m <= 32 ? 0 : m <= 64 ? 1 : m <= 128 ? 2 : 3; }
+// Levels per unit of a request: the table's G times 4, 2, 1, 1 by size class
+// (at most 16), so that a unit of small blocks carries about as many bytes as
+// one of m <= 128 and the claim, the wait and the fence are paid less often.
+__host__ __device__ inline int class_group(int G, int m) {
+  const int c = size_class(m);
+  const int g = G * (c == 0 ? 4 : c == 1 ? 2 : 1);
+  return g > 16 ? 16 : g;
+}
 
 struct BTable {
   int32_t n;            // active requests, ordered by size class
   int32_t cls_end[kClasses];     // requests [0, cls_end[c]) have size class <= c
   int32_t epoch;        // completion-counter base of this chunk
-  int32_t G;            // levels per unit of the fused sweep launches (1, 2 or 4)
+  int32_t G;            // levels per unit of the fused sweep launches (1, 2 or 4), scaled
+                        // per request by class_group
   int32_t pad;
   unsigned long long claim[kClasses];   // queue counters of one chunk's buckets (0 in t_host)
   int64_t off_h1[kMaxReq + 1];   // prefix counts of half-sweep-1 units (groups of G levels)

@@ -325,12 +325,13 @@ std::vector<Req*> build_table(mc_server* s) {
   t->G = s->G;
   t->off_h1[0] = t->off_h2[0] = t->off_lv[0] = 0;
   const int p1 = s->d.stair == 1 ? 0 : 1;
-  const int64_t G = s->G;
   for (int i = 0; i < t->n; ++i) {
     const Req* r = s->active[(size_t)i];
     const int64_t L = r->chain->lay.L;
     for (int c = cls(r); c < kClasses; ++c) t->cls_end[c] = i + 1;
     fill_req(s, r, &t->r[i]);
+    const int64_t G = class_group(s->G, r->chain->lay.m);
+    t->r[i].G = (int32_t)G;
     // units: groups of G levels of each half-sweep
     const int64_t P1 = (L - p1 + 1) / 2, P2 = (L - (1 - p1) + 1) / 2;
     t->off_h1[i + 1] = t->off_h1[i] + (P1 + G - 1) / G;
