@@ -225,15 +225,14 @@ static int enqueue_sweeps_fused(mc_chain* c, const double* src, double* dst, int
       a.rsum = rsum;
     }
     // block Gauss-Seidel runs at most min(K, L/2) units at once (one per sweep
-    // in flight); half as many warps again keep the next diagonal claimed
-    // without a crowd of warps spinning on later ones
+    // in flight), one block per unit; the launcher caps the grid at the blocks
+    // resident at once
     int nb = c->nb_fused;
-    if (c->tune_bps > 0 && c->tune_bps * c->num_sms < nb) nb = c->tune_bps * c->num_sms;
     if (a.bgs) {
       const int64_t par = K < (L + 1) / 2 ? K : (L + 1) / 2;
-      const int64_t nbw = (par + par / 2 + 32 + kWarpsPerBlock - 1) / kWarpsPerBlock;
-      if (nbw < nb) nb = (int)nbw;
+      nb = par < (1 << 30) ? (int)par : (1 << 30);
     }
+    if (c->tune_bps > 0 && c->tune_bps * c->num_sms < nb) nb = c->tune_bps * c->num_sms;
     CK(cudaMemsetAsync(c->fclaim, 0, cnt_bytes, s));
     CK(launch_sweeps_fused(a, coupled, nb, s));
     if (ev && final) CK(cudaEventRecord(ev[1], s));

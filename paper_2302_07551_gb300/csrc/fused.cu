@@ -136,30 +136,94 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs 
 // levels, and up to min(K, L / 2) units run at once.  In place in W (the
 // last sweep writes Z): a unit overwrites z^k_l only after its two readers,
 // (k, l-1) and (k-1, l+1), have completed, which is what it waits for.
+//
+// One block of kBgsWarps warps per unit: the warps split the columns of every
+// block product (warp w takes a fixed even-aligned column range and keeps
+// partial sums of all rows), and the partials are added in warp order.  A unit sits on the
+// wavefront's critical path, so streaming its blocks with 8 warps' loads in
+// flight instead of one shortens that path; the launch runs one block per
+// unit in flight.  Warp 0 waits for the two neighbours, the block barrier
+// hands the wait on (every warp also acquires both counters), and after its
+// stores every thread fences before thread 0 releases the level.  The
+// vectors sit in block shared memory with 16 zero doubles of padding, so a
+// warp's last column batch may read past its range (those products are with
+// zero block entries).
+constexpr int kBgsWarps = 8;
+
+__device__ __forceinline__ double bgs_parts(const double* part, int W, int i) {
+  return ((part[i] + part[W + i]) + (part[2 * W + i] + part[3 * W + i])) +
+         ((part[4 * W + i] + part[5 * W + i]) + (part[6 * W + i] + part[7 * W + i]));
+}
+
 template <int R, bool COUPLED>
-__global__ void __launch_bounds__(256, 2) k_bgs_fused(FusedArgs a) {
-  extern __shared__ double vsh[];
-  const int lane = threadIdx.x & 31;
-  double* slice = vsh + (threadIdx.x >> 5) * 3 * 32 * R;
+__global__ void __launch_bounds__(32 * kBgsWarps, 2) k_bgs_cta(FusedArgs a) {
+  constexpr int W = 32 * R, VS = W + 16;
+  extern __shared__ double sh[];
+  double* v_lo = sh;
+  double* v_up = sh + VS;
+  double* v_g = sh + 2 * VS;
+  double* part = sh + 3 * VS;   // kBgsWarps x W partial sums
+  __shared__ double red[kBgsWarps];
+  __shared__ unsigned long long s_q;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nt = blockDim.x;
+  const int m = a.m;
+  const int cw = (((m + kBgsWarps - 1) / kBgsWarps) + 1) & ~1;
+  const int j0 = w * cw, j1 = j0 + cw < m ? j0 + cw : m;
+  for (int i = threadIdx.x; i < 3 * VS; i += nt) sh[i] = 0.0;   // pads stay zero
   const unsigned long long total = (unsigned long long)a.K * (unsigned long long)a.L;
-  unsigned long long q0 = claim_unit(a.claim, lane);
-  unsigned long long q = __shfl_sync(kFull, q0, 0);
-  while (q < total) {
-    q0 = claim_unit(a.claim, lane);
+  while (true) {
+    if (threadIdx.x == 0) s_q = atomicAdd(a.claim, 1ull);
+    __syncthreads();
+    const unsigned long long q = s_q;
+    if (q >= total) break;
     int64_t k, l;
     wave_unit(q, a.L, a.K, &k, &l);
     double* dst = k == a.K - 1 ? a.Z : a.W;
     const double* up = k == 0 ? a.x_in : a.W;    // z^k at l + 1
-    wait_neighbours2(a.ver, l, a.L, (int)(k + 1), (int)k, &a.hdr->status, lane, a.wait_ns);
-    const bool want = k >= a.K - 2;
-    // few warps run (one per sweep in flight), each on the critical path:
-    // twice the columns per load batch, so a unit streams in half the round trips
-    const double t = level_sweep2<R, COUPLED, false, true, true, R <= 4 ? 2 : 1>(
-        a.A, a.B, a.C, dst, up, dst, l, a.L, a.m, a.ms, slice, lane, 1.0, nullptr, nullptr,
-        nullptr, want);
-    if (want && lane == 0) a.lsum[(k & 1) * a.L + l] = t;
-    publish(a.ver + l, (int)(k + 1), lane);
-    q = __shfl_sync(kFull, q0, 0);
+    const bool has_lo = l > 0, has_up = l < a.L - 1;
+    if (w == 0)
+      wait_neighbours2(a.ver, l, a.L, (int)(k + 1), (int)k, &a.hdr->status, lane, a.wait_ns);
+    __syncthreads();
+    if (w != 0) {
+      if (has_lo) (void)ld_acquire(a.ver + l - 1);
+      if (has_up && k > 0) (void)ld_acquire(a.ver + l + 1);
+    }
+    for (int i = threadIdx.x; i < m; i += nt) {
+      v_lo[i] = has_lo ? __ldcg(dst + (l - 1) * m + i) : 0.0;
+      v_up[i] = has_up ? __ldcg(up + (l + 1) * m + i) : 0.0;
+    }
+    __syncthreads();
+    double acc[R][Tune<R>::NA];
+    zero_acc<R>(acc);
+    if (j0 < j1) {
+      if (has_lo) gemv_acc_part<R, 0, R>(acc, a.A + (size_t)l * a.ms, v_lo, j0, j1, m, lane);
+      if (has_up) gemv_acc_part<R, 0, R>(acc, a.B + (size_t)l * a.ms, v_up, j0, j1, m, lane);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) part[w * W + lane + 32 * r] = fold<R>(acc[r]);
+    __syncthreads();
+    if (!COUPLED) {
+      for (int i = threadIdx.x; i < m; i += nt) v_g[i] = bgs_parts(part, W, i);
+      __syncthreads();
+      zero_acc<R>(acc);
+      if (j0 < j1) gemv_acc_part<R, 0, R>(acc, a.C + (size_t)l * a.ms, v_g, j0, j1, m, lane);
+#pragma unroll
+      for (int r = 0; r < R; ++r) part[w * W + lane + 32 * r] = fold<R>(acc[r]);
+      __syncthreads();
+    }
+    double ls = 0.0;
+    for (int i = threadIdx.x; i < m; i += nt) {
+      const double z = bgs_parts(part, W, i);
+      dst[l * m + i] = z;
+      ls += z;
+    }
+    if (k >= a.K - 2) {   // e^T z of the last two sweeps only (uniform over the block)
+      ls = block_sum(ls, red);
+      if (threadIdx.x == 0) a.lsum[(k & 1) * a.L + l] = ls;
+    }
+    __threadfence();
+    __syncthreads();   // every store of z_l, and every read of part, before the release
+    if (threadIdx.x == 0) st_release(a.ver + l, (int)(k + 1));
   }
 }
 
@@ -247,18 +311,25 @@ cudaError_t sweeps_r(const FusedArgs& a, int nb, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// nb: units that can run at once (capped here at the blocks resident at once,
+// so every claimed unit belongs to a running block).
 template <int R, bool C>
 cudaError_t bgs_fused_r(const FusedArgs& a, int nb, cudaStream_t s) {
-  static bool done = false;
-  const size_t smem = (size_t)kWarpsPerBlock * 3 * 32 * R * sizeof(double);
-  if (!done && smem > 40 * 1024) {
-    const cudaError_t e =
-        cudaFuncSetAttribute(k_bgs_fused<R, C>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+  static int cap = 0;
+  const size_t smem = (size_t)(3 * (32 * R + 16) + kBgsWarps * 32 * R) * sizeof(double);
+  if (cap == 0) {
+    int dev = 0, sms = 0, occ = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_bgs_cta<R, C>, 32 * kBgsWarps,
+                                                        smem);
     if (e != cudaSuccess) return e;
-    done = true;
+    cap = (occ < 1 ? 1 : occ) * sms;
   }
-  k_bgs_fused<R, C><<<nb, 256, smem, s>>>(a);
+  if (nb > cap) nb = cap;
+  if (nb < 1) nb = 1;
+  k_bgs_cta<R, C><<<nb, 32 * kBgsWarps, smem, s>>>(a);
   return cudaGetLastError();
 }
 

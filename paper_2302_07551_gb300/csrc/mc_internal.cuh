@@ -128,7 +128,7 @@ struct FusedArgs {
   // when K = 1).
   int with_resid;
   // block Gauss-Seidel instead of a stair splitting (block-tridiagonal, not
-  // paired): units in wavefront order, in place (k_bgs_fused)
+  // paired): units in wavefront order, in place (k_bgs_cta)
   int bgs;
   const double* RA;
   const double* RB;
