@@ -139,24 +139,30 @@ __global__ void __launch_bounds__(256, Tune<R>::MINB) k_sweeps_banded(FusedArgs 
 //
 // One block of kBgsWarps warps per unit: the warps split the columns of every
 // block product (warp w takes a fixed even-aligned column range and keeps
-// partial sums of all rows), and the partials are added in warp order.  A unit sits on the
-// wavefront's critical path, so streaming its blocks with 8 warps' loads in
-// flight instead of one shortens that path; the launch runs one block per
-// unit in flight.  Warp 0 waits for the two neighbours, the block barrier
+// partial sums of all rows), and the partials are added in warp order.  A
+// unit sits on the wavefront's critical path, so streaming its blocks with
+// several warps' loads in flight instead of one shortens that path; the
+// launch runs one block per unit in flight.  Four warps measured best (2, 4
+// and 8 tried: fewer warps per unit leave more units resident at once).  Warp 0 waits for the two neighbours, the block barrier
 // hands the wait on (every warp also acquires both counters), and after its
 // stores every thread fences before thread 0 releases the level.  The
 // vectors sit in block shared memory with 16 zero doubles of padding, so a
 // warp's last column batch may read past its range (those products are with
 // zero block entries).
-constexpr int kBgsWarps = 8;
+constexpr int kBgsWarps = 4;
 
 __device__ __forceinline__ double bgs_parts(const double* part, int W, int i) {
-  return ((part[i] + part[W + i]) + (part[2 * W + i] + part[3 * W + i])) +
-         ((part[4 * W + i] + part[5 * W + i]) + (part[6 * W + i] + part[7 * W + i]));
+  if constexpr (kBgsWarps == 8)
+    return ((part[i] + part[W + i]) + (part[2 * W + i] + part[3 * W + i])) +
+           ((part[4 * W + i] + part[5 * W + i]) + (part[6 * W + i] + part[7 * W + i]));
+  else if constexpr (kBgsWarps == 4)
+    return (part[i] + part[W + i]) + (part[2 * W + i] + part[3 * W + i]);
+  else
+    return part[i] + part[W + i];
 }
 
 template <int R, bool COUPLED>
-__global__ void __launch_bounds__(32 * kBgsWarps, 2) k_bgs_cta(FusedArgs a) {
+__global__ void __launch_bounds__(32 * kBgsWarps, 16 / kBgsWarps) k_bgs_cta(FusedArgs a) {
   constexpr int W = 32 * R, VS = W + 16;
   extern __shared__ double sh[];
   double* v_lo = sh;
