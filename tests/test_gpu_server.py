@@ -132,10 +132,12 @@ def test_bad_request_is_isolated():
 @pytest.mark.parametrize("dtype", ["f64", "bf16"])
 def test_autotuner_search_space_and_invariance(dtype):
     """The autotuner times live chunks over the persistent grid, the levels per
-    claimed unit (1, 2, 4), the block-size bucketing and (low precision, small
-    blocks) the load depth, keeps one configuration per batch signature, and
-    none of them changes a result: every request's pi is bitwise the one of an
-    untuned server, and matches the oracle."""
+    claimed unit (1, 2, 4 for m > 64; twice that for m <= 64, four times for
+    m <= 32), the block-size bucketing and (low precision, small blocks) the
+    load depth, keeps one configuration per batch signature, and none of them
+    changes a result: every request's pi is bitwise the one of an untuned
+    server (whose units already group 2 and 4 levels of the small blocks), and
+    matches the oracle."""
     mix = [(300, 16, 0.6), (257, 32, 0.8), (200, 64, 0.7), (120, 128, 0.9), (90, 64, 0.5)]
     out = {}
     for tune in (False, True):
